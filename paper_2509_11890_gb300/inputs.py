@@ -1,0 +1,257 @@
+"""Seeded synthetic inputs for the tensor-train SDP interior-point method.
+
+This module only draws graphs and weights. It holds none of the method's
+arithmetic (no TT rounding, no operator assembly, no IPM step): both the
+oracle and the CUDA path build everything else from what it returns, each
+with its own code.
+
+Workloads (all graphs on N = 2**d vertices, vertex u written big-endian in
+d binary digits, digit 1 most significant, as in the paper's vectorisation
+convention of Section 2.3):
+
+* ``kron_patterns`` / ``maxcut_kron``: the Kronecker graph. For each of the d
+  digits a symmetric 2x2 pattern B_k has entries p00, p01 = p10, p11 drawn
+  U[0, 1] in that order and thresholded at 0.5 to {0, 1}. The adjacency is
+  (B_1 kron ... kron B_d) with its diagonal zeroed; a draw without any edge is
+  rejected and the next draw of the same stream is used.
+* ``maxcut_kron_er``: the Kronecker graph OR-ed with an Erdos-Renyi graph
+  (each unordered pair u < v independently with probability 2/N), every
+  edge weighted U[0.5, 1.5], symmetric.
+* ``theta_hypercube_kron``: the d-cube Q_d OR-ed with a Kronecker graph,
+  accepted when the edge density lies in [0.8%, 1.5%].
+* ``cc_signed``: complete signed graph. W = sign(M + M^T) off the diagonal
+  (0 -> +1) for a rank-4 TT matrix M with N(0, 1) cores, then round(0.05 *
+  N(N-1)/2) seeded pairs u < v have their sign flipped (mirrored).
+* ``batch_maxcut``: many Kronecker Max-Cut instances with d drawn uniformly
+  from a range.
+
+Random streams come from numpy's Philox counter-based generator keyed by
+(seed, stream id), so every workload is reproducible from its seed alone.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "rng",
+    "kron_patterns",
+    "kron_dense",
+    "kron_adjacency_cores",
+    "maxcut_kron",
+    "maxcut_kron_er",
+    "theta_hypercube_kron",
+    "cc_signed",
+    "batch_maxcut",
+    "random_tt",
+    "random_tt_matrix",
+]
+
+# stream ids keep the draws of different workloads independent
+_STREAM_KRON = 1
+_STREAM_ER = 2
+_STREAM_WEIGHT = 3
+_STREAM_THETA = 4
+_STREAM_CC = 5
+_STREAM_CC_FLIP = 6
+_STREAM_BATCH = 7
+_STREAM_TT = 8
+
+
+def rng(seed: int, stream: int = 0) -> np.random.Generator:
+    """Philox generator keyed by (seed, stream)."""
+    return np.random.Generator(np.random.Philox(key=[int(seed) & (2**64 - 1), int(stream)]))
+
+
+def _draw_patterns(g: np.random.Generator, d: int) -> np.ndarray:
+    pats = np.zeros((d, 2, 2), dtype=np.int8)
+    for k in range(d):
+        p00, p01, p11 = g.uniform(0.0, 1.0, size=3)
+        pats[k] = [[p00 > 0.5, p01 > 0.5], [p01 > 0.5, p11 > 0.5]]
+    return pats
+
+
+def kron_dense(pats: np.ndarray) -> np.ndarray:
+    """Dense 0/1 adjacency (int8) of the Kronecker pattern graph, diagonal zeroed."""
+    a = np.ones((1, 1), dtype=np.int8)
+    for b in pats:
+        a = np.kron(a, b.astype(np.int8))
+    np.fill_diagonal(a, 0)
+    return a
+
+
+def _has_edge(pats: np.ndarray) -> bool:
+    # an off-diagonal entry of the Kronecker product is 1 iff every pattern
+    # has a 1 somewhere and at least one pattern has its off-diagonal 1
+    if any(int(b.sum()) == 0 for b in pats):
+        return False
+    return any(int(b[0, 1]) == 1 for b in pats)
+
+
+def kron_patterns(d: int, seed: int, stream: int = _STREAM_KRON) -> np.ndarray:
+    """The d seeded 2x2 0/1 patterns of a Kronecker graph with at least one edge."""
+    g = rng(seed, stream)
+    while True:
+        pats = _draw_patterns(g, d)
+        if _has_edge(pats):
+            return pats
+
+
+def kron_adjacency_cores(pats: np.ndarray) -> list[np.ndarray]:
+    """TT-matrix cores (r, 2, 2, r') of (kron_k B_k) - (kron_k diag(B_k)).
+
+    The second term removes the diagonal of the first, so the result is the
+    adjacency without self loops; its TT ranks are at most 2. The cores are
+    the plain block construction of a sum of two Kronecker products.
+    """
+    d = len(pats)
+    cores = []
+    for k, b in enumerate(pats):
+        bf = b.astype(np.float64)
+        db = np.diag(np.diag(bf))
+        if d == 1:
+            cores.append((bf - db).reshape(1, 2, 2, 1))
+        elif k == 0:
+            c = np.zeros((1, 2, 2, 2))
+            c[0, :, :, 0] = bf
+            c[0, :, :, 1] = -db
+            cores.append(c)
+        elif k == d - 1:
+            c = np.zeros((2, 2, 2, 1))
+            c[0, :, :, 0] = bf
+            c[1, :, :, 0] = db
+            cores.append(c)
+        else:
+            c = np.zeros((2, 2, 2, 2))
+            c[0, :, :, 0] = bf
+            c[1, :, :, 1] = db
+            cores.append(c)
+    return cores
+
+
+def maxcut_kron(d: int, seed: int) -> dict:
+    """Unit-weight Max-Cut instance on a seeded Kronecker graph."""
+    pats = kron_patterns(d, seed)
+    adj = kron_dense(pats)
+    return {
+        "kind": "maxcut",
+        "d": d,
+        "seed": seed,
+        "patterns": pats,
+        "adjacency": adj,
+        "weights": adj.astype(np.float64),
+        "adjacency_cores": kron_adjacency_cores(pats),
+    }
+
+
+def maxcut_kron_er(d: int, seed: int, p_scale: float = 2.0) -> dict:
+    """Kronecker graph OR Erdos-Renyi(p_scale / N), weights U[0.5, 1.5]."""
+    n = 2**d
+    pats = kron_patterns(d, seed)
+    adj = kron_dense(pats).astype(bool)
+    g = rng(seed, _STREAM_ER)
+    er = np.triu(g.random((n, n)) < (p_scale / n), k=1)
+    adj |= er | er.T
+    np.fill_diagonal(adj, False)
+    gw = rng(seed, _STREAM_WEIGHT)
+    w = np.triu(gw.uniform(0.5, 1.5, size=(n, n)), k=1)
+    w = w + w.T
+    weights = np.where(adj, w, 0.0)
+    return {
+        "kind": "maxcut",
+        "d": d,
+        "seed": seed,
+        "patterns": pats,
+        "adjacency": adj.astype(np.int8),
+        "weights": weights,
+        "adjacency_cores": None,
+    }
+
+
+def hypercube_dense(d: int) -> np.ndarray:
+    n = 2**d
+    u = np.arange(n)
+    x = u[:, None] ^ u[None, :]
+    return ((x > 0) & ((x & (x - 1)) == 0)).astype(np.int8)
+
+
+def theta_hypercube_kron(d: int, seed: int, lo: float = 0.008, hi: float = 0.015) -> dict:
+    """Lovasz-theta instance: Q_d OR a Kronecker graph with density in [lo, hi]."""
+    n = 2**d
+    q = hypercube_dense(d).astype(bool)
+    g_stream = 0
+    while True:
+        pats = kron_patterns(d, seed, stream=_STREAM_THETA * 1000 + g_stream)
+        adj = q | kron_dense(pats).astype(bool)
+        np.fill_diagonal(adj, False)
+        dens = adj.sum() / (n * (n - 1))
+        if lo <= dens <= hi or d < 6:
+            break
+        g_stream += 1
+    return {
+        "kind": "theta",
+        "d": d,
+        "seed": seed,
+        "patterns": pats,
+        "adjacency": adj.astype(np.int8),
+        "weights": adj.astype(np.float64),
+        "adjacency_cores": None,
+        "density": float(dens),
+    }
+
+
+def random_tt(dims: list[int], ranks: list[int], seed: int, stream: int = _STREAM_TT) -> list[np.ndarray]:
+    """TT-vector cores (r_k, n_k, r_k+1) with N(0, 1) entries."""
+    g = rng(seed, stream)
+    return [g.standard_normal((ranks[k], dims[k], ranks[k + 1])) for k in range(len(dims))]
+
+
+def random_tt_matrix(rows: list[int], cols: list[int], ranks: list[int], seed: int,
+                     stream: int = _STREAM_TT) -> list[np.ndarray]:
+    """TT-matrix cores (r_k, m_k, n_k, r_k+1) with N(0, 1) entries."""
+    g = rng(seed, stream)
+    return [g.standard_normal((ranks[k], rows[k], cols[k], ranks[k + 1])) for k in range(len(rows))]
+
+
+def _tt_matrix_dense(cores: list[np.ndarray]) -> np.ndarray:
+    # plain reconstruction used only to draw the sign pattern of cc_signed
+    full = np.ones((1, 1, 1))
+    for c in cores:
+        r, m, n, r2 = c.shape
+        full = np.einsum("xya,aijb->xiyjb", full, c)
+        full = full.reshape(full.shape[0] * m, full.shape[2] * n, r2)
+    return full[:, :, 0]
+
+
+def cc_signed(d: int, seed: int, flip_frac: float = 0.05) -> dict:
+    """Correlation-clustering instance on the complete signed graph."""
+    n = 2**d
+    ranks = [1] + [4] * (d - 1) + [1]
+    m = _tt_matrix_dense(random_tt_matrix([2] * d, [2] * d, ranks, seed, stream=_STREAM_CC))
+    s = m + m.T
+    w = np.where(s >= 0.0, 1.0, -1.0)
+    iu, ju = np.triu_indices(n, k=1)
+    nflip = int(round(flip_frac * len(iu)))
+    g = rng(seed, _STREAM_CC_FLIP)
+    pick = g.choice(len(iu), size=nflip, replace=False)
+    w[iu[pick], ju[pick]] *= -1.0
+    w[ju[pick], iu[pick]] *= -1.0
+    np.fill_diagonal(w, 0.0)
+    adj = np.ones((n, n), dtype=np.int8)
+    np.fill_diagonal(adj, 0)
+    return {
+        "kind": "cc",
+        "d": d,
+        "seed": seed,
+        "adjacency": adj,
+        "weights": w,
+        "c_plus": np.where(w > 0, w, 0.0),
+        "c_minus": np.where(w < 0, -w, 0.0),
+        "adjacency_cores": None,
+    }
+
+
+def batch_maxcut(count: int, seed: int, d_lo: int = 6, d_hi: int = 11) -> list[dict]:
+    """`count` Kronecker Max-Cut instances with d ~ U{d_lo..d_hi}."""
+    g = rng(seed, _STREAM_BATCH)
+    ds = g.integers(d_lo, d_hi + 1, size=count)
+    return [maxcut_kron(int(dd), seed * 100003 + i) for i, dd in enumerate(ds)]
