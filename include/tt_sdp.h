@@ -1,0 +1,260 @@
+/*
+ * tt_sdp.h -- C ABI of the GB300 tensor-train SDP interior-point library.
+ *
+ * The library implements the inexact tensor-train primal-dual interior-point
+ * method for semidefinite programs of Kelbel, Dolgov, Kalise and Russo
+ * ("An Inexact Tensor-Train Primal-Dual Interior-Point Method for
+ * Semidefinite Programs"): the SDP variables X, Y, [T], Z and the constraint
+ * operators are tensor trains with 2 x 2 modes per core (operators on the
+ * vec_TT space have 4 x 4 modes), the Newton direction of the tensorised KKT
+ * system (Section 3.3, eq. tt-kkt-newton-system) is found by block-AMEn with
+ * matrix-free local products, and iterates are kept at moderate rank by TT
+ * rounding with a spectral shift (Section 3.4, Corollary psdness_rounding).
+ *
+ * Conventions shared by every call.
+ *  - TT vector cores are row-major [r_k][m][r_{k+1}], TT matrix cores
+ *    [r_k][m][n][r_{k+1}], r_0 = r_d = 1, concatenated core after core
+ *    (Section 2.3, Definitions "Tensor-Train" and "TT Matrix").
+ *  - Multi-indices are big-endian (digit 1 most significant) and vec_TT
+ *    interleaves (row digit, column digit) with the row digit more
+ *    significant (Section 3.1, Definition "TT Vectorisation" and its
+ *    worked example); a 2 x 2 matrix mode (i, j) maps to vector mode 2 i + j.
+ *  - All arithmetic on device pointers is ordered on the CUDA stream passed
+ *    in (NULL: the legacy default stream). Calls return after their results
+ *    are usable on that stream; calls that return host values synchronise it.
+ *  - Errors are status codes; nothing else crosses the boundary. A call that
+ *    fails leaves its outputs unspecified and the library usable.
+ *  - No CPU fallback: without a CUDA device every call returns TT_E_CUDA.
+ */
+#ifndef TT_SDP_H
+#define TT_SDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_E_INVALID_ARG = 1,    /* null pointer, negative size, unknown enum value       */
+  TT_E_SHAPE = 2,          /* ranks / modes inconsistent between operands           */
+  TT_E_NOMEM = 3,          /* device allocation failed or output capacity too small */
+  TT_E_CUDA = 4,           /* CUDA runtime error (message via tt_last_error)        */
+  TT_E_NOT_PD = 5,         /* an iterate lost positive definiteness (Section 3.4)   */
+  TT_E_RANK_CAP = 6,       /* warning: rank cap bound with truncation error > tol   */
+  TT_E_NO_CONVERGENCE = 7, /* iteration or sweep budget exhausted                   */
+  TT_E_TIMEOUT = 8,        /* a bounded device wait gave up                         */
+  TT_E_NUMERIC = 9,        /* NaN or Inf detected                                   */
+  TT_E_INTERNAL = 10
+} tt_status;
+
+/* Arithmetic used by the contractions (environments, local products). */
+typedef enum {
+  TT_FP64 = 0,        /* everything in FP64                                          */
+  TT_FP32 = 1,        /* FP32 SIMT contractions, FP32 accumulation                   */
+  TT_MIXED_TF32 = 2,  /* TF32 tensor-core contractions, FP32 accumulation            */
+  TT_MIXED_BF16 = 3   /* BF16 tensor-core contractions, FP32 accumulation            */
+} tt_precision;
+
+/* Dimensions of one three-operand contraction step (Section 3.3, the
+ * matrix-free local products with cached environments):
+ *   frame core   U [rw][m][rw2]
+ *   operator core Op [R][m][n][R2]   (TT matrix on the vec_TT space)
+ *   vector core  V [rv][n][rv2]
+ * A left environment Phi has shape [rw][R][rv], a right one Psi [rw2][R2][rv2]. */
+typedef struct {
+  int32_t rw, rw2;
+  int32_t R, R2;
+  int32_t rv, rv2;
+  int32_t m, n;
+} tt_contract_dims;
+
+/* ---------------------------------------------------------------------------
+ * Contraction kernels (rows a6, a7 of the hot path). Device pointers, FP64
+ * storage; `precision` selects the arithmetic. Outputs are caller-allocated.
+ * ------------------------------------------------------------------------- */
+
+/* Left environment update (Section 3.3, local products with cached
+ * environments): out[b'][q][b] = sum U[a'][i][b'] Op[p][i][j][q] V[a][j][b] Phi[a'][p][a].
+ * out holds rw2 * R2 * rv2 doubles. */
+tt_status tt_env_left_step(const tt_contract_dims* dims, const double* phi, const double* u,
+                           const double* op, const double* v, double* out, int32_t precision,
+                           void* stream);
+
+/* Right environment update: out[a'][p][a] = sum U[a'][i][b'] Op[p][i][j][q] V[a][j][b] Psi[b'][q][b].
+ * out holds rw * R * rv doubles. */
+tt_status tt_env_right_step(const tt_contract_dims* dims, const double* psi, const double* u,
+                            const double* op, const double* v, double* out, int32_t precision,
+                            void* stream);
+
+/* Local matrix-free product (Section 3.3, "inserting the local GMRES vector
+ * into the active core"): y[a'][i][b'] = sum Phi[a'][p][a] Op[p][i][j][q] Psi[b'][q][b] x[a][j][b].
+ * Here rv = rw-side size of x's left rank and rv2 its right rank;
+ * x holds rv * n * rv2 doubles, y holds rw * m * rw2. */
+tt_status tt_local_apply(const tt_contract_dims* dims, const double* phi, const double* op,
+                         const double* psi, const double* x, double* y, int32_t precision,
+                         void* stream);
+
+/* Dense projected operator W^T Op W at one core: out[(a',i,b')][(a,j,b)],
+ * (rw*m*rw2) x (rv*n*rv2) row-major doubles. */
+tt_status tt_local_matrix(const tt_contract_dims* dims, const double* phi, const double* op,
+                          const double* psi, double* out, int32_t precision, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * TT-level operations on device cores (rows a3, a8, a9). A tt_desc names
+ * device cores here; ranks are host arrays.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t d;              /* number of cores                                    */
+  const int32_t* ranks;   /* host array, d + 1 entries, ranks[0] = ranks[d] = 1 */
+  int32_t m, n;           /* modes of every core; n = 1 for TT vectors          */
+  const double* cores;    /* concatenated cores (device or host, per call)      */
+} tt_desc;
+
+/* Number of doubles in the cores of a TT with the given ranks and modes. */
+size_t tt_core_count(int32_t d, const int32_t* ranks, int32_t m, int32_t n);
+
+/* Element-wise (Hadamard) product of two TTs with equal modes, the product
+ * of the Remark after Definition "TT Diagonalisation" (Section 3.3):
+ * core [(a,x)][mode][(b,y)] = A[a][mode][b] B[x][mode][y]; ranks multiply.
+ * out holds tt_core_count(d, ra*rb, m, n) doubles. */
+tt_status tt_hadamard(const tt_desc* a, const tt_desc* b, double* out, void* stream);
+
+/* TT matrix times TT vector, core [(p,a)][i][(q,b)] = sum_j Op[p][i][j][q] V[a][j][b]
+ * (diag_TT operators reduce this to the masked products of Section 3.3). */
+tt_status tt_matvec(const tt_desc* op, const tt_desc* v, double* out, void* stream);
+
+/* Inner product <a, b> over all entries (a3): one environment sweep. The
+ * result is written to *out (host) and the stream is synchronised. */
+tt_status tt_inner(const tt_desc* a, const tt_desc* b, double* out, void* stream);
+
+/* TT rounding (row a9; Oseledets' round_TT as used in Section 2.3):
+ * right-to-left Householder QR, then left-to-right truncated SVD. Bond k
+ * keeps the smallest rank whose discarded energy is <= (delta/sqrt(d-1))^2,
+ * then at most rank_cap (<= 0: no cap). ranks_out (host, d+1), cores_out
+ * (device, capacity doubles >= input count). *zeta_out (host) receives
+ * ||T - round(T)||_F = sqrt(sum of all discarded sigma^2). The input is a
+ * TT vector view (set m to the full mode size, n = 1). */
+tt_status tt_round(const tt_desc* in, double delta, int32_t rank_cap, int32_t* ranks_out,
+                   double* cores_out, size_t capacity, double* zeta_out, int32_t precision,
+                   void* stream);
+
+/* ---------------------------------------------------------------------------
+ * The solver (rows a1-a5, a10-a12): a context holds one SDP in TT form and
+ * its iterates on the device.
+ * ------------------------------------------------------------------------- */
+
+/* Tensorised SDP of Section 3.1:
+ *   max <C, X>  s.t.  A_eq vec_TT(X) = B_eq,  A_ineq vec_TT(X) >= / <= B_ineq,  X psd,
+ * with the idle-multiplier masks K_y, K_t of Section 3.3. All descriptors
+ * name HOST cores; they are copied at create. Operators have m = n = 4,
+ * right-hand sides m = 4, n = 1, C and ones_t m = n = 2. Absent parts have d = 0. */
+typedef struct {
+  tt_desc C;
+  tt_desc A_eq;
+  tt_desc B_eq;
+  tt_desc K_y;
+  tt_desc A_ineq;
+  tt_desc B_ineq;
+  tt_desc K_t;
+  tt_desc ones_t;      /* 1_T: ones on the non-idle inequality positions            */
+  int32_t ineq_sign;   /* +1: s = A_ineq x - B_ineq >= 0 (Section 4.3); -1: <=       */
+  int64_t q;           /* number of inequality entries in mirrored storage          */
+  double lam0;         /* initial scale lambda* (Section 5.1)                        */
+  double lam0_ineq;    /* lambda*_ineq                                               */
+} tt_sdp_problem;
+
+typedef struct {
+  double eps_gap;      /* target; eps_p = eps_d = 2 eps_gap, eps_c = eps_gap / sqrt(d) */
+  int32_t rank_cap;    /* cap on iterate and direction TT ranks                        */
+  int32_t xz_warmup;   /* iterations with the XZ direction before AHO (3)              */
+  double eta0;         /* initial forcing term (1e-3)                                  */
+  double eta_floor;    /* delta of the forcing schedule (1e-4)                         */
+  double eta_C;        /* C of eta <- max(min(eta, C mu), delta) (2)                   */
+  double damping;      /* step damping factor (0.95)                                   */
+  int32_t precision;   /* tt_precision of the contractions                             */
+  int32_t max_iters;
+  int32_t max_sweeps;  /* AMEn sweeps per Newton solve                                 */
+  int32_t kick;        /* AMEn random enrichment columns                               */
+  int32_t eig_rank;    /* TT rank of the step-length eigenvector                       */
+  int32_t eig_sweeps;
+  uint64_t seed;       /* SplitMix64 counter stream seed                               */
+} tt_sdp_options;
+
+typedef struct tt_sdp_ctx tt_sdp_ctx;
+
+typedef struct {
+  int32_t iter;
+  int32_t converged;   /* 1 when the stopping rules of Section 3.5 hold              */
+  double mu, rel_p, rel_d, rel_gap, pobj, dobj, alpha_p, alpha_d;
+  int32_t max_rank_X, max_rank_Z, max_rank_W, sweeps;
+  int32_t direction;   /* 0 XZ, 1 AHO                                                 */
+  double seconds;      /* device time of the iteration (CUDA events)                 */
+} tt_sdp_iter_info;
+
+typedef struct {
+  tt_status status;
+  int32_t iters;
+  double pobj, dobj, rel_gap, rel_p, rel_d, seconds;
+} tt_sdp_result;
+
+/* Defaults of Section 5.1 (eps_gap 1e-4, 3 XZ warm-up iterations, eta0 1e-3,
+ * eta floor 1e-4, C = 2) and of this library (damping 0.95, kick 4, ...). */
+void tt_sdp_default_options(tt_sdp_options* opts);
+
+/* Copies the problem to the device and sets the initial point of Section 5.1:
+ * X = Z = lam0 I, Y = 0 (with inequalities X = lam0 I + (alpha_p/10) 1_T,
+ * T = lam0_ineq 1_T). */
+tt_status tt_sdp_create(const tt_sdp_problem* prob, const tt_sdp_options* opts, void* stream,
+                        tt_sdp_ctx** out);
+
+/* Row a1: assemble the Section 4 formulations on the device from the graph
+ * adjacency given as a host TT matrix (2 x 2 modes, zero diagonal) and create
+ * the context. Max-Cut (Section 4.1) uses `weights` (the weighted adjacency;
+ * pass the adjacency for unit weights); theta (Section 4.2) the adjacency;
+ * correlation clustering (Section 4.3) C+ and C- and the adjacency. */
+tt_status tt_sdp_create_maxcut(const tt_desc* weights, const tt_sdp_options* opts, void* stream,
+                               tt_sdp_ctx** out);
+tt_status tt_sdp_create_theta(const tt_desc* adjacency, const tt_sdp_options* opts, void* stream,
+                              tt_sdp_ctx** out);
+tt_status tt_sdp_create_cc(const tt_desc* c_plus, const tt_desc* c_minus, const tt_desc* adjacency,
+                           const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out);
+
+/* One iteration of Algorithm 1 (residuals, mu, Mehrotra predictor and
+ * corrector Newton solves, step lengths, update and rounding). Returns
+ * TT_OK with info->converged = 1 when the stopping rules already hold. */
+tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info);
+
+/* Iterates until the stopping rules hold or max_iters. */
+tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out);
+
+/* Copies iterate `which` (0 X, 1 Y, 2 T, 3 Z; TT matrices with 2 x 2 modes)
+ * to the host. With cores == NULL only ranks (d+1 ints) and *count are set. */
+tt_status tt_sdp_get_iterate(tt_sdp_ctx* ctx, int32_t which, int32_t* ranks, double* cores,
+                             size_t* count);
+
+/* Number of cores d of the context's problem. */
+int32_t tt_sdp_order(const tt_sdp_ctx* ctx);
+
+void tt_sdp_destroy(tt_sdp_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics
+ * ------------------------------------------------------------------------- */
+const char* tt_sdp_status_string(tt_status s);
+/* Message of the last failure on the calling thread (empty if none). */
+const char* tt_last_error(void);
+/* Kernels launched by the library since load (monotone counter). */
+uint64_t tt_launch_count(void);
+/* Device time spent in the contraction kernels since the last reset, and
+ * their algorithmic flop count (for the contraction TFLOP/s metric). */
+void tt_contraction_stats(double* flops, double* seconds);
+void tt_contraction_stats_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TT_SDP_H */

@@ -13,8 +13,9 @@ Conventions (Section 2.3, Definitions "Tensor-Train", "TT Matrix"):
   Section 3.1 fixes this); vec_TT interleaves (alpha_k, beta_k) with alpha_k
   the more significant digit (Definition "TT Vectorisation").
 
-Everything here is deliberately naive: explicit einsum contractions, numpy QR
-and SVD as library steps, no blocking or fusion.
+Everything here is deliberately plain: einsum contractions (numpy picks the
+pairwise evaluation order of each sum), numpy QR and SVD as library steps, no
+blocking or fusion.
 """
 from __future__ import annotations
 
@@ -302,7 +303,7 @@ def inner(u: list[np.ndarray], v: list[np.ndarray]) -> float:
         rv, rv2 = cv.shape[0], cv.shape[-1]
         a = cu.reshape(ru, -1, ru2)
         b = cv.reshape(rv, -1, rv2)
-        phi = np.einsum("ax,aib,xiy->by", phi, a, b)
+        phi = np.einsum("ax,aib,xiy->by", phi, a, b, optimize=True)
     return float(phi[0, 0])
 
 
@@ -345,14 +346,24 @@ def frame(cores: list[np.ndarray], k: int) -> np.ndarray:
 # ----------------------------------------------------------------------------
 
 
+# The local products are evaluated as the three successive matrix products the
+# paper's cost statement for the matrix-free local product describes
+# (Section 3.3): contract over the vector rank, then over (operator rank,
+# mode), then over the frame rank and mode. Each step is one tensordot.
+
+
 def env_left_step(phi: np.ndarray, u: np.ndarray, op: np.ndarray, v: np.ndarray) -> np.ndarray:
     """Phi'[b', q, b] = sum U[a', i, b'] Op[p, i, j, q] V[a, j, b] Phi[a', p, a]."""
-    return np.einsum("xpa,xiy,pijq,ajb->yqb", phi, u, op, v)
+    t1 = np.tensordot(phi, v, axes=([2], [0]))          # [a', p, j, b]
+    t2 = np.tensordot(t1, op, axes=([1, 2], [0, 2]))     # [a', b, i, q]
+    return np.tensordot(u, t2, axes=([0, 1], [0, 2])).transpose(0, 2, 1).copy()  # [b', q, b]
 
 
 def env_right_step(psi: np.ndarray, u: np.ndarray, op: np.ndarray, v: np.ndarray) -> np.ndarray:
     """Psi'[a', p, a] = sum U[a', i, b'] Op[p, i, j, q] V[a, j, b] Psi[b', q, b]."""
-    return np.einsum("yqb,xiy,pijq,ajb->xpa", psi, u, op, v)
+    t1 = np.tensordot(v, psi, axes=([2], [2]))           # [a, j, b', q]
+    t2 = np.tensordot(t1, op, axes=([1, 3], [2, 3]))     # [a, b', p, i]
+    return np.tensordot(u, t2, axes=([1, 2], [3, 1])).transpose(0, 2, 1).copy()  # [a', p, a]
 
 
 def envs_left(u: list[np.ndarray], op: list[np.ndarray], v: list[np.ndarray]) -> list[np.ndarray]:
@@ -375,14 +386,18 @@ def envs_right(u: list[np.ndarray], op: list[np.ndarray], v: list[np.ndarray]) -
 
 def local_apply(phi: np.ndarray, op: np.ndarray, psi: np.ndarray, x: np.ndarray) -> np.ndarray:
     """y[a', i, b'] = sum Phi[a', p, a] Op[p, i, j, q] Psi[b', q, b] x[a, j, b]."""
-    return np.einsum("xpa,pijq,yqb,ajb->xiy", phi, op, psi, x)
+    t1 = np.tensordot(phi, x, axes=([2], [0]))           # [a', p, j, b]
+    t2 = np.tensordot(t1, op, axes=([1, 2], [0, 2]))     # [a', b, i, q]
+    return np.tensordot(t2, psi, axes=([3, 1], [1, 2])).copy()  # [a', i, b']
 
 
 def local_matrix(phi: np.ndarray, op: np.ndarray, psi: np.ndarray) -> np.ndarray:
     """Dense projected operator, rows (a', i, b'), columns (a, j, b)."""
-    m = np.einsum("xpa,pijq,yqb->xiyajb", phi, op, psi)
+    t1 = np.tensordot(phi, op, axes=([1], [0]))          # [a', a, i, j, q]
+    m = np.tensordot(t1, psi, axes=([4], [1]))           # [a', a, i, j, b', b]
+    m = m.transpose(0, 2, 4, 1, 3, 5)
     s = m.shape
-    return m.reshape(s[0] * s[1] * s[2], s[3] * s[4] * s[5])
+    return m.reshape(s[0] * s[1] * s[2], s[3] * s[4] * s[5]).copy()
 
 
 def local_matrix_by_frame(u: list[np.ndarray], op: list[np.ndarray], v: list[np.ndarray], k: int) -> np.ndarray:
@@ -455,5 +470,5 @@ def round_tt(cores: list[np.ndarray], delta: float, cap: int | None = None):
             keep = cap
         zeta2 += float(np.sum(s[keep:] ** 2))
         c[k] = u[:, :keep].reshape(r, n, keep)
-        c[k + 1] = np.einsum("a,ab,bjc->ajc", s[:keep], vt[:keep], c[k + 1])
+        c[k + 1] = np.einsum("a,ab,bjc->ajc", s[:keep], vt[:keep], c[k + 1], optimize=True)
     return c, math.sqrt(zeta2), ties

@@ -1,0 +1,282 @@
+"""GB300 tensor-train SDP interior-point library: Python binding.
+
+Every function here marshals arguments into the C ABI of include/tt_sdp.h;
+all arithmetic runs in the CUDA library. Device tensors are torch CUDA
+tensors (float64, contiguous); host TT cores are lists of numpy arrays.
+Importing the package does not load the library; the first call does, and
+fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+FP64, FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
+
+__all__ = [
+    "FP64", "FP32", "MIXED_TF32", "MIXED_BF16", "TTSDPError", "lib",
+    "env_left_step", "env_right_step", "local_apply", "local_matrix",
+    "hadamard", "matvec", "inner", "round_tt", "default_options", "Context",
+    "launch_count", "contraction_stats", "contraction_stats_reset",
+]
+
+
+class TTSDPError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib_ = _lib.load()
+        msg = lib_.tt_sdp_status_string(status).decode()
+        detail = lib_.tt_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}) {detail}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    return _lib.load()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise TTSDPError(status, where)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _dims(d) -> _lib.ContractDims:
+    if isinstance(d, dict):
+        return _lib.ContractDims(d["rw"], d["rw2"], d["R"], d["R2"], d["rv"], d["rv2"], d["m"], d["n"])
+    return _lib.ContractDims(*d)
+
+
+# --- contraction kernels (rows a6, a7) ---------------------------------------
+
+def env_left_step(dims, phi, u, op, v, out, precision=FP64, stream=None):
+    dm = _dims(dims)
+    _check(lib().tt_env_left_step(ctypes.byref(dm), _ptr(phi), _ptr(u), _ptr(op), _ptr(v), _ptr(out), precision,
+                                  _stream(stream)), "tt_env_left_step")
+
+
+def env_right_step(dims, psi, u, op, v, out, precision=FP64, stream=None):
+    dm = _dims(dims)
+    _check(lib().tt_env_right_step(ctypes.byref(dm), _ptr(psi), _ptr(u), _ptr(op), _ptr(v), _ptr(out), precision,
+                                   _stream(stream)), "tt_env_right_step")
+
+
+def local_apply(dims, phi, op, psi, x, y, precision=FP64, stream=None):
+    dm = _dims(dims)
+    _check(lib().tt_local_apply(ctypes.byref(dm), _ptr(phi), _ptr(op), _ptr(psi), _ptr(x), _ptr(y), precision,
+                                _stream(stream)), "tt_local_apply")
+
+
+def local_matrix(dims, phi, op, psi, out, precision=FP64, stream=None):
+    dm = _dims(dims)
+    _check(lib().tt_local_matrix(ctypes.byref(dm), _ptr(phi), _ptr(op), _ptr(psi), _ptr(out), precision,
+                                 _stream(stream)), "tt_local_matrix")
+
+
+# --- TT-level operations (rows a3, a8, a9) ------------------------------------
+
+class DevTT:
+    """A TT whose cores live in one flat float64 CUDA tensor."""
+
+    def __init__(self, ranks, m, n, flat):
+        self.ranks = [int(r) for r in ranks]
+        self.m, self.n = int(m), int(n)
+        self.flat = flat
+
+    @property
+    def d(self):
+        return len(self.ranks) - 1
+
+    @staticmethod
+    def from_cores(cores, device="cuda"):
+        import torch
+        c0 = cores[0]
+        m = c0.shape[1]
+        n = c0.shape[2] if c0.ndim == 4 else 1
+        ranks = [c.shape[0] for c in cores] + [cores[-1].shape[-1]]
+        flat = np.concatenate([np.ascontiguousarray(c, dtype=np.float64).reshape(-1) for c in cores])
+        return DevTT(ranks, m, n, torch.from_numpy(flat).to(device))
+
+    def cores(self):
+        flat = self.flat.detach().cpu().numpy()
+        out, off = [], 0
+        for k in range(self.d):
+            shape = (self.ranks[k], self.m, self.n, self.ranks[k + 1]) if self.n > 1 else \
+                (self.ranks[k], self.m, self.ranks[k + 1])
+            size = int(np.prod(shape))
+            out.append(flat[off:off + size].reshape(shape).copy())
+            off += size
+        return out
+
+    def desc(self):
+        self._r = (ctypes.c_int32 * len(self.ranks))(*self.ranks)
+        return _lib.TTDesc(self.d, ctypes.cast(self._r, _lib.P_int32), self.m, self.n, _ptr(self.flat))
+
+
+def _count(ranks, m, n):
+    return sum(ranks[k] * m * n * ranks[k + 1] for k in range(len(ranks) - 1))
+
+
+def hadamard(a: DevTT, b: DevTT, stream=None) -> DevTT:
+    import torch
+    ranks = [x * y for x, y in zip(a.ranks, b.ranks)]
+    out = torch.empty(_count(ranks, a.m, a.n), dtype=torch.float64, device=a.flat.device)
+    da, db = a.desc(), b.desc()
+    _check(lib().tt_hadamard(ctypes.byref(da), ctypes.byref(db), _ptr(out), _stream(stream)), "tt_hadamard")
+    return DevTT(ranks, a.m, a.n, out)
+
+
+def matvec(op: DevTT, v: DevTT, stream=None) -> DevTT:
+    import torch
+    ranks = [x * y for x, y in zip(op.ranks, v.ranks)]
+    out = torch.empty(_count(ranks, op.m, 1), dtype=torch.float64, device=op.flat.device)
+    da, db = op.desc(), v.desc()
+    _check(lib().tt_matvec(ctypes.byref(da), ctypes.byref(db), _ptr(out), _stream(stream)), "tt_matvec")
+    return DevTT(ranks, op.m, 1, out)
+
+
+def inner(a: DevTT, b: DevTT, stream=None) -> float:
+    res = ctypes.c_double(0.0)
+    da, db = a.desc(), b.desc()
+    _check(lib().tt_inner(ctypes.byref(da), ctypes.byref(db), ctypes.byref(res), _stream(stream)), "tt_inner")
+    return res.value
+
+
+def round_tt(a: DevTT, delta: float, cap: int = 0, stream=None):
+    """TT rounding of the vector view of `a`; returns (DevTT, zeta)."""
+    import torch
+    v = DevTT(a.ranks, a.m * a.n, 1, a.flat)
+    out = torch.empty(a.flat.numel(), dtype=torch.float64, device=a.flat.device)
+    ranks = (ctypes.c_int32 * (a.d + 1))()
+    zeta = ctypes.c_double(0.0)
+    dv = v.desc()
+    _check(lib().tt_round(ctypes.byref(dv), float(delta), int(cap), ranks, _ptr(out), out.numel(),
+                          ctypes.byref(zeta), FP64, _stream(stream)), "tt_round")
+    rr = list(ranks)
+    return DevTT(rr, a.m, a.n, out[:_count(rr, a.m * a.n, 1)].clone()), zeta.value
+
+
+# --- the solver (rows a1-a5, a10-a12) ----------------------------------------
+
+def default_options(**kw) -> _lib.Options:
+    o = _lib.Options()
+    lib().tt_sdp_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class _HostTT:
+    """Host cores packed for a tt_desc (kept alive with the descriptor)."""
+
+    def __init__(self, cores, m, n):
+        self.flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).reshape(-1) for c in cores]))
+        ranks = [c.shape[0] for c in cores] + [cores[-1].shape[-1]]
+        self.r = (ctypes.c_int32 * len(ranks))(*ranks)
+        self.desc = _lib.TTDesc(len(cores), ctypes.cast(self.r, _lib.P_int32), m, n,
+                                self.flat.ctypes.data_as(ctypes.c_void_p))
+
+
+class Context:
+    """One SDP in TT form with its iterates on the device (tt_sdp_ctx)."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    @staticmethod
+    def maxcut(weight_cores, options=None, stream=None):
+        w = _HostTT(weight_cores, 2, 2)
+        o = options or default_options()
+        h = ctypes.c_void_p()
+        _check(lib().tt_sdp_create_maxcut(ctypes.byref(w.desc), ctypes.byref(o), _stream(stream), ctypes.byref(h)),
+               "tt_sdp_create_maxcut")
+        return Context(h, [w])
+
+    @staticmethod
+    def theta(adj_cores, options=None, stream=None):
+        a = _HostTT(adj_cores, 2, 2)
+        o = options or default_options()
+        h = ctypes.c_void_p()
+        _check(lib().tt_sdp_create_theta(ctypes.byref(a.desc), ctypes.byref(o), _stream(stream), ctypes.byref(h)),
+               "tt_sdp_create_theta")
+        return Context(h, [a])
+
+    @staticmethod
+    def cc(c_plus_cores, c_minus_cores, adj_cores, options=None, stream=None):
+        p, m, a = _HostTT(c_plus_cores, 2, 2), _HostTT(c_minus_cores, 2, 2), _HostTT(adj_cores, 2, 2)
+        o = options or default_options()
+        h = ctypes.c_void_p()
+        _check(lib().tt_sdp_create_cc(ctypes.byref(p.desc), ctypes.byref(m.desc), ctypes.byref(a.desc),
+                                      ctypes.byref(o), _stream(stream), ctypes.byref(h)), "tt_sdp_create_cc")
+        return Context(h, [p, m, a])
+
+    def newton_step(self) -> dict:
+        info = _lib.IterInfo()
+        _check(lib().tt_sdp_newton_step(self._h, ctypes.byref(info)), "tt_sdp_newton_step")
+        return {f: getattr(info, f) for f, _ in _lib.IterInfo._fields_}
+
+    def solve(self) -> dict:
+        res = _lib.Result()
+        st = lib().tt_sdp_solve(self._h, ctypes.byref(res))
+        out = {f: getattr(res, f) for f, _ in _lib.Result._fields_}
+        if st not in (0, 7):
+            _check(st, "tt_sdp_solve")
+        return out
+
+    def iterate(self, which: int):
+        """Cores (host numpy, r x 2 x 2 x r') of X (0), Y (1), T (2) or Z (3)."""
+        d = lib().tt_sdp_order(self._h)
+        ranks = (ctypes.c_int32 * (d + 1))()
+        cnt = ctypes.c_size_t(0)
+        _check(lib().tt_sdp_get_iterate(self._h, which, ranks, None, ctypes.byref(cnt)), "tt_sdp_get_iterate")
+        buf = np.empty(cnt.value, dtype=np.float64)
+        _check(lib().tt_sdp_get_iterate(self._h, which, ranks, buf.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.byref(cnt)), "tt_sdp_get_iterate")
+        r = list(ranks)
+        out, off = [], 0
+        for k in range(d):
+            size = r[k] * 4 * r[k + 1]
+            out.append(buf[off:off + size].reshape(r[k], 2, 2, r[k + 1]).copy())
+            off += size
+        return out
+
+    def close(self):
+        if self._h:
+            lib().tt_sdp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launch_count() -> int:
+    return int(lib().tt_launch_count())
+
+
+def contraction_stats():
+    f, s = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    lib().tt_contraction_stats(ctypes.byref(f), ctypes.byref(s))
+    return f.value, s.value
+
+
+def contraction_stats_reset():
+    lib().tt_contraction_stats_reset()

@@ -1,0 +1,104 @@
+"""ctypes declarations of the C ABI in include/tt_sdp.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libttsdp.so")
+
+c_int32 = ctypes.c_int32
+c_double = ctypes.c_double
+c_size_t = ctypes.c_size_t
+c_void_p = ctypes.c_void_p
+P_int32 = ctypes.POINTER(c_int32)
+P_double = ctypes.POINTER(c_double)
+
+
+class ContractDims(ctypes.Structure):
+    _fields_ = [("rw", c_int32), ("rw2", c_int32), ("R", c_int32), ("R2", c_int32),
+                ("rv", c_int32), ("rv2", c_int32), ("m", c_int32), ("n", c_int32)]
+
+
+class TTDesc(ctypes.Structure):
+    _fields_ = [("d", c_int32), ("ranks", P_int32), ("m", c_int32), ("n", c_int32), ("cores", c_void_p)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("C", TTDesc), ("A_eq", TTDesc), ("B_eq", TTDesc), ("K_y", TTDesc),
+                ("A_ineq", TTDesc), ("B_ineq", TTDesc), ("K_t", TTDesc), ("ones_t", TTDesc),
+                ("ineq_sign", c_int32), ("q", ctypes.c_int64), ("lam0", c_double), ("lam0_ineq", c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eps_gap", c_double), ("rank_cap", c_int32), ("xz_warmup", c_int32),
+                ("eta0", c_double), ("eta_floor", c_double), ("eta_C", c_double), ("damping", c_double),
+                ("precision", c_int32), ("max_iters", c_int32), ("max_sweeps", c_int32), ("kick", c_int32),
+                ("eig_rank", c_int32), ("eig_sweeps", c_int32), ("seed", ctypes.c_uint64)]
+
+
+class IterInfo(ctypes.Structure):
+    _fields_ = [("iter", c_int32), ("converged", c_int32), ("mu", c_double), ("rel_p", c_double),
+                ("rel_d", c_double), ("rel_gap", c_double), ("pobj", c_double), ("dobj", c_double),
+                ("alpha_p", c_double), ("alpha_d", c_double), ("max_rank_X", c_int32), ("max_rank_Z", c_int32),
+                ("max_rank_W", c_int32), ("sweeps", c_int32), ("direction", c_int32), ("seconds", c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("iters", c_int32), ("pobj", c_double), ("dobj", c_double),
+                ("rel_gap", c_double), ("rel_p", c_double), ("rel_d", c_double), ("seconds", c_double)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/tt_sdp.h
+SIGNATURES = {
+    "tt_env_left_step": (c_int32, [ctypes.POINTER(ContractDims), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_int32, c_void_p]),
+    "tt_env_right_step": (c_int32, [ctypes.POINTER(ContractDims), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_int32, c_void_p]),
+    "tt_local_apply": (c_int32, [ctypes.POINTER(ContractDims), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 c_int32, c_void_p]),
+    "tt_local_matrix": (c_int32, [ctypes.POINTER(ContractDims), c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                  c_void_p]),
+    "tt_core_count": (c_size_t, [c_int32, P_int32, c_int32, c_int32]),
+    "tt_hadamard": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), c_void_p, c_void_p]),
+    "tt_matvec": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), c_void_p, c_void_p]),
+    "tt_inner": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), P_double, c_void_p]),
+    "tt_round": (c_int32, [ctypes.POINTER(TTDesc), c_double, c_int32, P_int32, c_void_p, c_size_t, P_double,
+                           c_int32, c_void_p]),
+    "tt_sdp_default_options": (None, [ctypes.POINTER(Options)]),
+    "tt_sdp_create": (c_int32, [ctypes.POINTER(Problem), ctypes.POINTER(Options), c_void_p, ctypes.POINTER(c_void_p)]),
+    "tt_sdp_create_maxcut": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(Options), c_void_p,
+                                       ctypes.POINTER(c_void_p)]),
+    "tt_sdp_create_theta": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(Options), c_void_p,
+                                      ctypes.POINTER(c_void_p)]),
+    "tt_sdp_create_cc": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc),
+                                   ctypes.POINTER(Options), c_void_p, ctypes.POINTER(c_void_p)]),
+    "tt_sdp_newton_step": (c_int32, [c_void_p, ctypes.POINTER(IterInfo)]),
+    "tt_sdp_solve": (c_int32, [c_void_p, ctypes.POINTER(Result)]),
+    "tt_sdp_get_iterate": (c_int32, [c_void_p, c_int32, P_int32, c_void_p, ctypes.POINTER(c_size_t)]),
+    "tt_sdp_order": (c_int32, [c_void_p]),
+    "tt_sdp_destroy": (None, [c_void_p]),
+    "tt_sdp_status_string": (ctypes.c_char_p, [c_int32]),
+    "tt_last_error": (ctypes.c_char_p, []),
+    "tt_launch_count": (ctypes.c_uint64, []),
+    "tt_contraction_stats": (None, [P_double, P_double]),
+    "tt_contraction_stats_reset": (None, []),
+}
+
+_LIB = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads the compiled library; raises if it is missing (there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib

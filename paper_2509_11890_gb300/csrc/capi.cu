@@ -1,0 +1,396 @@
+// extern "C" boundary: argument checking, stream scoping and the conversion
+// of library exceptions into status codes.
+#include <cstring>
+#include <string>
+
+#include "contract.cuh"
+#include "solver.cuh"
+#include "tt.cuh"
+
+using namespace ttsdp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct StreamGuard {
+  cudaStream_t prev;
+  explicit StreamGuard(void* s) : prev(StreamScope::current()) { StreamScope::current() = (cudaStream_t)s; }
+  ~StreamGuard() { StreamScope::current() = prev; }
+};
+
+template <typename F>
+tt_status guarded(void* stream, F&& fn) {
+  try {
+    StreamGuard g(stream);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      g_last_error = "no CUDA device";
+      return TT_E_CUDA;
+    }
+    fn();
+    g_last_error.clear();
+    return TT_OK;
+  } catch (const TTError& e) {
+    g_last_error = e.what();
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return TT_E_NOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return TT_E_INTERNAL;
+  }
+}
+
+CDims to_cdims(const tt_contract_dims* d) {
+  TT_CHECK(d != nullptr, TT_E_INVALID_ARG, "null dims");
+  TT_CHECK(d->rw > 0 && d->rw2 > 0 && d->R > 0 && d->R2 > 0 && d->rv > 0 && d->rv2 > 0 && d->m > 0 && d->n > 0,
+           TT_E_SHAPE, "dimensions must be positive");
+  return CDims{d->rw, d->rw2, d->R, d->R2, d->rv, d->rv2, d->m, d->n};
+}
+
+void check_desc(const tt_desc* a) {
+  TT_CHECK(a && a->d > 0 && a->ranks && a->cores && a->m > 0 && a->n > 0, TT_E_INVALID_ARG, "bad tt_desc");
+}
+
+DTT desc_dev(const tt_desc* a) {
+  check_desc(a);
+  return tt_from_device(a->d, a->ranks, a->m, a->n, a->cores);
+}
+
+DTT desc_host(const tt_desc* a) {
+  check_desc(a);
+  return tt_from_host(a->d, a->ranks, a->m, a->n, a->cores);
+}
+
+Options to_options(const tt_sdp_options* o) {
+  Options r;
+  if (!o) return r;
+  r.eps_gap = o->eps_gap;
+  r.rank_cap = o->rank_cap;
+  r.xz_warmup = o->xz_warmup;
+  r.eta0 = o->eta0;
+  r.eta_floor = o->eta_floor;
+  r.eta_C = o->eta_C;
+  r.damping = o->damping;
+  r.prec = o->precision;
+  r.max_iters = o->max_iters;
+  r.max_sweeps = o->max_sweeps;
+  r.kick = o->kick;
+  r.eig_rank = o->eig_rank;
+  r.eig_sweeps = o->eig_sweeps;
+  r.seed = o->seed;
+  TT_CHECK(r.rank_cap > 0 && r.max_sweeps > 0 && r.eig_sweeps > 0 && r.eig_rank > 0 && r.kick >= 0,
+           TT_E_INVALID_ARG, "invalid options");
+  TT_CHECK(r.prec >= TT_FP64 && r.prec <= TT_MIXED_BF16, TT_E_INVALID_ARG, "unknown precision");
+  return r;
+}
+
+}  // namespace
+
+struct tt_sdp_ctx {
+  cudaStream_t stream;
+  std::unique_ptr<Solver> solver;
+};
+
+extern "C" {
+
+const char* tt_sdp_status_string(tt_status s) {
+  switch (s) {
+    case TT_OK: return "ok";
+    case TT_E_INVALID_ARG: return "invalid argument";
+    case TT_E_SHAPE: return "shape mismatch";
+    case TT_E_NOMEM: return "out of memory";
+    case TT_E_CUDA: return "CUDA error";
+    case TT_E_NOT_PD: return "iterate not positive definite";
+    case TT_E_RANK_CAP: return "rank cap bound";
+    case TT_E_NO_CONVERGENCE: return "no convergence";
+    case TT_E_TIMEOUT: return "device wait timed out";
+    case TT_E_NUMERIC: return "non-finite value";
+    case TT_E_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+const char* tt_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t tt_launch_count(void) { return LaunchCounter::value(); }
+
+void tt_contraction_stats(double* flops, double* seconds) {
+  try {
+    stats_read(flops, seconds);
+  } catch (...) {
+    if (flops) *flops = 0;
+    if (seconds) *seconds = 0;
+  }
+}
+
+void tt_contraction_stats_reset(void) {
+  try {
+    stats_reset();
+  } catch (...) {
+  }
+}
+
+size_t tt_core_count(int32_t d, const int32_t* ranks, int32_t m, int32_t n) {
+  if (d <= 0 || !ranks) return 0;
+  size_t s = 0;
+  for (int k = 0; k < d; ++k) s += (size_t)ranks[k] * m * n * ranks[k + 1];
+  return s;
+}
+
+tt_status tt_env_left_step(const tt_contract_dims* dims, const double* phi, const double* u, const double* op,
+                           const double* v, double* out, int32_t precision, void* stream) {
+  return guarded(stream, [&] {
+    CDims c = to_cdims(dims);
+    TT_CHECK(phi && u && op && v && out, TT_E_INVALID_ARG, "null pointer");
+    env_left_step(c, phi, u, op, v, out, precision, cur_stream());
+  });
+}
+
+tt_status tt_env_right_step(const tt_contract_dims* dims, const double* psi, const double* u, const double* op,
+                            const double* v, double* out, int32_t precision, void* stream) {
+  return guarded(stream, [&] {
+    CDims c = to_cdims(dims);
+    TT_CHECK(psi && u && op && v && out, TT_E_INVALID_ARG, "null pointer");
+    env_right_step(c, psi, u, op, v, out, precision, cur_stream());
+  });
+}
+
+tt_status tt_local_apply(const tt_contract_dims* dims, const double* phi, const double* op, const double* psi,
+                         const double* x, double* y, int32_t precision, void* stream) {
+  return guarded(stream, [&] {
+    CDims c = to_cdims(dims);
+    TT_CHECK(phi && op && psi && x && y, TT_E_INVALID_ARG, "null pointer");
+    local_apply(c, phi, op, psi, x, y, precision, cur_stream());
+  });
+}
+
+tt_status tt_local_matrix(const tt_contract_dims* dims, const double* phi, const double* op, const double* psi,
+                          double* out, int32_t precision, void* stream) {
+  return guarded(stream, [&] {
+    CDims c = to_cdims(dims);
+    TT_CHECK(phi && op && psi && out, TT_E_INVALID_ARG, "null pointer");
+    local_matrix(c, phi, op, psi, out, precision, cur_stream());
+  });
+}
+
+tt_status tt_hadamard(const tt_desc* a, const tt_desc* b, double* out, void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(out, TT_E_INVALID_ARG, "null output");
+    DTT r = tt_hadamard(desc_dev(a), desc_dev(b));
+    tt_to_device(r, out);
+  });
+}
+
+tt_status tt_matvec(const tt_desc* op, const tt_desc* v, double* out, void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(out, TT_E_INVALID_ARG, "null output");
+    DTT r = tt_matvec(desc_dev(op), desc_dev(v));
+    tt_to_device(r, out);
+  });
+}
+
+tt_status tt_inner(const tt_desc* a, const tt_desc* b, double* out, void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(out, TT_E_INVALID_ARG, "null output");
+    *out = tt_inner(desc_dev(a), desc_dev(b));
+  });
+}
+
+tt_status tt_round(const tt_desc* in, double delta, int32_t rank_cap, int32_t* ranks_out, double* cores_out,
+                   size_t capacity, double* zeta_out, int32_t precision, void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(ranks_out && cores_out && zeta_out && delta >= 0.0, TT_E_INVALID_ARG, "bad tt_round arguments");
+    TT_CHECK(precision == TT_FP64, TT_E_INVALID_ARG, "rounding runs in FP64");
+    DTT a = desc_dev(in);
+    auto rz = tt_round(a, delta, rank_cap);
+    TT_CHECK(rz.first.count() <= capacity, TT_E_NOMEM, "output capacity too small");
+    tt_to_device(rz.first, cores_out);
+    for (int k = 0; k <= rz.first.d; ++k) ranks_out[k] = rz.first.r[k];
+    *zeta_out = rz.second;
+    TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  });
+}
+
+void tt_sdp_default_options(tt_sdp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eps_gap = 1e-4;
+  o->rank_cap = 16;
+  o->xz_warmup = 3;
+  o->eta0 = 1e-3;
+  o->eta_floor = 1e-4;
+  o->eta_C = 2.0;
+  o->damping = 0.95;
+  o->precision = TT_FP64;
+  o->max_iters = 60;
+  o->max_sweeps = 4;
+  o->kick = 4;
+  o->eig_rank = 4;
+  o->eig_sweeps = 4;
+  o->seed = 1234;
+}
+
+static tt_status make_ctx(Problem p, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
+  return guarded(stream, [&] {
+    TT_CHECK(out, TT_E_INVALID_ARG, "null output");
+    Options o = to_options(opts);
+    auto* ctx = new tt_sdp_ctx;
+    ctx->stream = (cudaStream_t)stream;
+    try {
+      ctx->solver = std::make_unique<Solver>(std::move(p), o);
+    } catch (...) {
+      delete ctx;
+      throw;
+    }
+    *out = ctx;
+  });
+}
+
+tt_status tt_sdp_create(const tt_sdp_problem* prob, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
+  Problem p;
+  tt_status s = guarded(stream, [&] {
+    TT_CHECK(prob, TT_E_INVALID_ARG, "null problem");
+    p.d = prob->C.d;
+    p.C = desc_host(&prob->C);
+    p.A_eq = desc_host(&prob->A_eq);
+    p.B_eq = desc_host(&prob->B_eq);
+    p.K_y = desc_host(&prob->K_y);
+    TT_CHECK(p.C.m == 2 && p.C.n == 2 && p.A_eq.m == 4 && p.A_eq.n == 4 && p.B_eq.m == 4 && p.K_y.m == 4,
+             TT_E_SHAPE, "problem modes");
+    TT_CHECK(p.A_eq.d == p.d && p.B_eq.d == p.d && p.K_y.d == p.d, TT_E_SHAPE, "problem orders differ");
+    if (prob->A_ineq.d > 0) {
+      p.ineq = true;
+      p.A_ineq = desc_host(&prob->A_ineq);
+      p.B_ineq = desc_host(&prob->B_ineq);
+      p.K_t = desc_host(&prob->K_t);
+      p.ones_t = desc_host(&prob->ones_t);
+      p.sgn = prob->ineq_sign >= 0 ? 1.0 : -1.0;
+      p.q = prob->q;
+    }
+    p.lam0 = prob->lam0 > 0 ? prob->lam0 : 1.0;
+    p.lam0_ineq = prob->lam0_ineq > 0 ? prob->lam0_ineq : 1e-3;
+  });
+  if (s != TT_OK) return s;
+  return make_ctx(std::move(p), opts, stream, out);
+}
+
+tt_status tt_sdp_create_maxcut(const tt_desc* weights, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
+  Problem p;
+  tt_status s = guarded(stream, [&] {
+    TT_CHECK(weights && weights->m == 2 && weights->n == 2, TT_E_SHAPE, "weights must have 2 x 2 modes");
+    p = build_maxcut(desc_host(weights));
+  });
+  if (s != TT_OK) return s;
+  return make_ctx(std::move(p), opts, stream, out);
+}
+
+tt_status tt_sdp_create_theta(const tt_desc* adjacency, const tt_sdp_options* opts, void* stream,
+                              tt_sdp_ctx** out) {
+  Problem p;
+  tt_status s = guarded(stream, [&] {
+    TT_CHECK(adjacency && adjacency->m == 2 && adjacency->n == 2, TT_E_SHAPE, "adjacency must have 2 x 2 modes");
+    p = build_theta(desc_host(adjacency));
+  });
+  if (s != TT_OK) return s;
+  return make_ctx(std::move(p), opts, stream, out);
+}
+
+tt_status tt_sdp_create_cc(const tt_desc* c_plus, const tt_desc* c_minus, const tt_desc* adjacency,
+                           const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
+  Problem p;
+  tt_status s = guarded(stream, [&] {
+    for (const tt_desc* t : {c_plus, c_minus, adjacency})
+      TT_CHECK(t && t->m == 2 && t->n == 2, TT_E_SHAPE, "inputs must have 2 x 2 modes");
+    p = build_cc(desc_host(c_plus), desc_host(c_minus), desc_host(adjacency));
+  });
+  if (s != TT_OK) return s;
+  return make_ctx(std::move(p), opts, stream, out);
+}
+
+tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info) {
+  if (!ctx || !info) return TT_E_INVALID_ARG;
+  return guarded(ctx->stream, [&] {
+    IterLog l = ctx->solver->iterate();
+    info->iter = l.iter;
+    info->converged = l.converged;
+    info->mu = l.mu;
+    info->rel_p = l.rel_p;
+    info->rel_d = l.rel_d;
+    info->rel_gap = l.rel_gap;
+    info->pobj = l.pobj;
+    info->dobj = l.dobj;
+    info->alpha_p = l.alpha_p;
+    info->alpha_d = l.alpha_d;
+    info->max_rank_X = l.max_rank_X;
+    info->max_rank_Z = l.max_rank_Z;
+    info->max_rank_W = l.max_rank_W;
+    info->sweeps = l.sweeps;
+    info->direction = l.direction;
+    info->seconds = l.seconds;
+  });
+}
+
+tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out) {
+  if (!ctx || !out) return TT_E_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  tt_sdp_iter_info info;
+  double secs = 0.0;
+  const int max_iters = ctx->solver->options().max_iters;
+  for (int it = 0; it <= max_iters; ++it) {
+    tt_status s = tt_sdp_newton_step(ctx, &info);
+    if (s != TT_OK) {
+      out->status = s;
+      return s;
+    }
+    secs += info.seconds;
+    out->iters = info.iter;
+    out->pobj = info.pobj;
+    out->dobj = info.dobj;
+    out->rel_gap = info.rel_gap;
+    out->rel_p = info.rel_p;
+    out->rel_d = info.rel_d;
+    out->seconds = secs;
+    if (info.converged) {
+      out->status = TT_OK;
+      return TT_OK;
+    }
+  }
+  out->status = TT_E_NO_CONVERGENCE;
+  return TT_E_NO_CONVERGENCE;
+}
+
+tt_status tt_sdp_get_iterate(tt_sdp_ctx* ctx, int32_t which, int32_t* ranks, double* cores, size_t* count) {
+  if (!ctx || !ranks || !count) return TT_E_INVALID_ARG;
+  return guarded(ctx->stream, [&] {
+    TT_CHECK(which >= 0 && which <= 3, TT_E_INVALID_ARG, "which must be 0..3");
+    TT_CHECK(which != 2 || ctx->solver->has_ineq(), TT_E_INVALID_ARG, "no inequality multiplier");
+    const DTT& t = which == 0 ? ctx->solver->X() : which == 1 ? ctx->solver->Y()
+                                                  : which == 2 ? ctx->solver->T() : ctx->solver->Z();
+    for (int k = 0; k <= t.d; ++k) ranks[k] = t.r[k];
+    size_t need = t.count();
+    if (cores) {
+      TT_CHECK(*count >= need, TT_E_NOMEM, "capacity too small");
+      tt_to_host(t, cores);
+    }
+    *count = need;
+  });
+}
+
+int32_t tt_sdp_order(const tt_sdp_ctx* ctx) { return ctx ? ctx->solver->order() : 0; }
+
+void tt_sdp_destroy(tt_sdp_ctx* ctx) {
+  if (!ctx) return;
+  try {
+    StreamGuard g(ctx->stream);
+    ctx->solver.reset();
+    cudaStreamSynchronize(ctx->stream);
+  } catch (...) {
+  }
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Shared device plumbing for the TT-SDP library: status codes, error
+// propagation, stream-ordered device buffers and small host helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/tt_sdp.h"
+
+namespace ttsdp {
+
+// Every failure inside the library is thrown as TTError and converted to a
+// status code at the C boundary; nothing crosses the ABI as an exception.
+struct TTError : public std::runtime_error {
+  tt_status status;
+  TTError(tt_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define TT_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      throw ::ttsdp::TTError(TT_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TT_CHECK(cond, st, msg)                     \
+  do {                                              \
+    if (!(cond)) throw ::ttsdp::TTError(st, msg);   \
+  } while (0)
+
+inline void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw TTError(TT_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// The library's single ordered stream (set by the context or per call).
+struct StreamScope {
+  static cudaStream_t& current() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+  }
+};
+inline cudaStream_t cur_stream() { return StreamScope::current(); }
+
+// Device buffer allocated stream-ordered from the device's default memory pool.
+template <typename T>
+class DBuf {
+ public:
+  DBuf() = default;
+  explicit DBuf(size_t n) { alloc(n); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p_(o.p_), n_(o.n_) { o.p_ = nullptr; o.n_ = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p_ = o.p_; n_ = o.n_; o.p_ = nullptr; o.n_ = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t n) {
+    release();
+    n_ = n;
+    if (n) TT_CUDA(cudaMallocAsync((void**)&p_, n * sizeof(T), cur_stream()));
+  }
+  void release() {
+    if (p_) cudaFreeAsync(p_, cur_stream());
+    p_ = nullptr;
+    n_ = 0;
+  }
+  T* get() const { return p_; }
+  size_t size() const { return n_; }
+
+ private:
+  T* p_ = nullptr;
+  size_t n_ = 0;
+};
+
+// Counts kernel launches issued by the library (reported by the benchmark).
+struct LaunchCounter {
+  static unsigned long long& value() {
+    static unsigned long long v = 0;
+    return v;
+  }
+};
+inline void count_launch() { ++LaunchCounter::value(); }
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace ttsdp

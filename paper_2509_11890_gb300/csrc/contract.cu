@@ -1,0 +1,382 @@
+// Environment updates, local products and projected matrices as three
+// strided GEMM stages on the cores' natural row-major layouts:
+//   stage 1  contract the environment with the vector core over its rank,
+//   stage 2  contract with the operator core over (operator rank, mode),
+//   stage 3  contract with the frame core (or the other environment).
+// FP64 runs the stages in FP64; FP32 converts the operands once and runs
+// the same stages in FP32 with FP32 accumulation.
+#include <mutex>
+
+#include "contract.cuh"
+#include "gemm.cuh"
+#include "tc_gemm.cuh"
+
+namespace ttsdp {
+
+namespace {
+
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long s = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += s) b[i] = (float)a[i];
+}
+__global__ void to_double_kernel(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long s = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += s) b[i] = (double)a[i];
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)(g < 152 * 16 ? (g < 1 ? 1 : g) : 152 * 16);
+}
+
+}  // namespace
+
+void to_float(const double* a, float* b, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  to_float_kernel<<<grid_for(n), 256, 0, st>>>(a, b, n);
+  count_launch();
+  check_launch("to_float");
+}
+void to_double(const float* a, double* b, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  to_double_kernel<<<grid_for(n), 256, 0, st>>>(a, b, n);
+  count_launch();
+  check_launch("to_double");
+}
+
+double contract_flops(const CDims& d) {
+  double s1 = 2.0 * d.rw * d.R * d.rv * d.n * d.rv2;
+  double s2 = 2.0 * d.rw * d.rv2 * (double)(d.R * d.n) * (double)(d.m * d.R2);
+  double s3 = 2.0 * d.rw2 * d.R2 * d.rv2 * (double)(d.rw * d.m);
+  return s1 + s2 + s3;
+}
+
+// ---------------------------------------------------------------------------
+// typed implementations
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static void env_left_t(const CDims& d, const T* phi, const T* u, const T* op, const T* v, T* out,
+                       T* t1, T* t2, cudaStream_t st, int prec) {
+  const long long rw = d.rw, rw2 = d.rw2, R = d.R, R2 = d.R2, rv = d.rv, rv2 = d.rv2, m = d.m,
+                  n = d.n;
+  const size_t nphi = rw * R * rv, nu = rw * m * rw2, nop = R * m * n * R2, nv = rv * n * rv2;
+  const size_t nt1 = rw * R * n * rv2, nt2 = rw * m * R2 * rv2, nout = rw2 * R2 * rv2;
+  // stage 1: T1[a'][p][j][b] = sum_a Phi[a'][p][a] V[a][j][b]
+  {
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)(rw * R), rv, n * rv2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)(n * rv2), 1, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)rv, 1, n * rv2}});
+    set_batch(g, {});
+    gemm_nd<T>(g, phi, nphi, v, nv, t1, nt1, T(1), T(0), st);
+  }
+  // stage 2: T2[a'][i][q][b] = sum_{p,j} Op[p][i][j][q] T1[a'][p][j][b]
+  if (!tc_stage2<T>(prec, rw, R, R2, m, n, rv2, op, t1, t2, st)) {
+    GemmND g;
+    set_batch(g, {{(int)rw, 0, R * n * rv2, m * R2 * rv2}});
+    set_dim(g.M, g.aM, g.cM, {{(int)m, n * R2, R2 * rv2}, {(int)R2, 1, rv2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)rv2, 1, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)R, m * n * R2, n * rv2}, {(int)n, R2, rv2}});
+    gemm_nd<T>(g, op, nop, t1, nt1, t2, nt2, T(1), T(0), st);
+  }
+  // stage 3: out[b'][q][b] = sum_{a',i} U[a'][i][b'] T2[a'][i][q][b]
+  {
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)rw2, 1, R2 * rv2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)(R2 * rv2), 1, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)(rw * m), rw2, R2 * rv2}});
+    set_batch(g, {});
+    gemm_nd<T>(g, u, nu, t2, nt2, out, nout, T(1), T(0), st);
+  }
+}
+
+template <typename T>
+static void env_right_t(const CDims& d, const T* psi, const T* u, const T* op, const T* v, T* out,
+                        T* t1, T* t2, cudaStream_t st) {
+  const long long rw = d.rw, rw2 = d.rw2, R = d.R, R2 = d.R2, rv = d.rv, rv2 = d.rv2, m = d.m,
+                  n = d.n;
+  const size_t npsi = rw2 * R2 * rv2, nu = rw * m * rw2, nop = R * m * n * R2, nv = rv * n * rv2;
+  const size_t nt1 = rv * n * rw2 * R2, nt2 = rv * R * m * rw2, nout = rw * R * rv;
+  // stage 1: T1[a][j][b'][q] = sum_b V[a][j][b] Psi[b'][q][b]
+  {
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)(rv * n), rv2, rw2 * R2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)(rw2 * R2), rv2, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)rv2, 1, 1}});
+    set_batch(g, {});
+    gemm_nd<T>(g, v, nv, psi, npsi, t1, nt1, T(1), T(0), st);
+  }
+  // stage 2: T2[a][p][i][b'] = sum_{j,q} Op[p][i][j][q] T1[a][j][b'][q]
+  {
+    GemmND g;
+    set_batch(g, {{(int)rv, 0, n * rw2 * R2, R * m * rw2}});
+    set_dim(g.M, g.aM, g.cM, {{(int)(R * m), n * R2, rw2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)rw2, R2, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)n, R2, rw2 * R2}, {(int)R2, 1, 1}});
+    gemm_nd<T>(g, op, nop, t1, nt1, t2, nt2, T(1), T(0), st);
+  }
+  // stage 3: out[a'][p][a] = sum_{i,b'} U[a'][i][b'] T2[a][p][i][b']
+  {
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)rw, m * rw2, R * rv}});
+    set_dim(g.N, g.bN, g.cN, {{(int)R, m * rw2, rv}, {(int)rv, R * m * rw2, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)(m * rw2), 1, 1}});
+    set_batch(g, {});
+    gemm_nd<T>(g, u, nu, t2, nt2, out, nout, T(1), T(0), st);
+  }
+}
+
+template <typename T>
+static void apply_t(const CDims& d, const T* phi, const T* op, const T* psi, const T* x, T* y,
+                    T* t1, T* t2, cudaStream_t st, int prec) {
+  const long long rw = d.rw, rw2 = d.rw2, R = d.R, R2 = d.R2, rv = d.rv, rv2 = d.rv2, m = d.m,
+                  n = d.n;
+  const size_t nphi = rw * R * rv, npsi = rw2 * R2 * rv2, nop = R * m * n * R2, nx = rv * n * rv2;
+  const size_t nt1 = rw * R * n * rv2, nt2 = rw * m * R2 * rv2, ny = rw * m * rw2;
+  {
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)(rw * R), rv, n * rv2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)(n * rv2), 1, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)rv, 1, n * rv2}});
+    set_batch(g, {});
+    gemm_nd<T>(g, phi, nphi, x, nx, t1, nt1, T(1), T(0), st);
+  }
+  if (!tc_stage2<T>(prec, rw, R, R2, m, n, rv2, op, t1, t2, st)) {
+    GemmND g;
+    set_batch(g, {{(int)rw, 0, R * n * rv2, m * R2 * rv2}});
+    set_dim(g.M, g.aM, g.cM, {{(int)m, n * R2, R2 * rv2}, {(int)R2, 1, rv2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)rv2, 1, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)R, m * n * R2, n * rv2}, {(int)n, R2, rv2}});
+    gemm_nd<T>(g, op, nop, t1, nt1, t2, nt2, T(1), T(0), st);
+  }
+  // stage 3: y[a'][i][b'] = sum_{q,b} T2[a'][i][q][b] Psi[b'][q][b]
+  {
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)(rw * m), R2 * rv2, rw2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)rw2, R2 * rv2, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)(R2 * rv2), 1, 1}});
+    set_batch(g, {});
+    gemm_nd<T>(g, t2, nt2, psi, npsi, y, ny, T(1), T(0), st);
+  }
+}
+
+template <typename T>
+static void local_matrix_t(const CDims& d, const T* phi, const T* op, const T* psi, T* out, T* t1,
+                           cudaStream_t st) {
+  const long long rw = d.rw, rw2 = d.rw2, R = d.R, R2 = d.R2, rv = d.rv, rv2 = d.rv2, m = d.m,
+                  n = d.n;
+  const long long nloc = rv * n * rv2;
+  const size_t nphi = rw * R * rv, npsi = rw2 * R2 * rv2, nop = R * m * n * R2;
+  const size_t nt1 = rw * rv * m * n * R2, nout = (size_t)(rw * m * rw2) * nloc;
+  // stage 1: T1[a'][a][i][j][q] = sum_p Phi[a'][p][a] Op[p][i][j][q]
+  {
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)rw, R * rv, rv * m * n * R2}, {(int)rv, 1, m * n * R2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)(m * n * R2), 1, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)R, rv, m * n * R2}});
+    set_batch(g, {});
+    gemm_nd<T>(g, phi, nphi, op, nop, t1, nt1, T(1), T(0), st);
+  }
+  // stage 2: out[(a',i,b')][(a,j,b)] = sum_q Psi[b'][q][b] T1[a'][a][i][j][q]
+  {
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)rw2, R2 * rv2, nloc}, {(int)rv2, 1, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)R2, rv2, 1}});
+    set_dim(g.N, g.bN, g.cN,
+            {{(int)rw, rv * m * n * R2, m * rw2 * nloc},
+             {(int)m, n * R2, rw2 * nloc},
+             {(int)rv, m * n * R2, n * rv2},
+             {(int)n, R2, rv2}});
+    set_batch(g, {});
+    gemm_nd<T>(g, psi, npsi, t1, nt1, out, nout, T(1), T(0), st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// precision dispatch
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct F32Scratch {
+  DBuf<float> a, b, c, d, e, t1, t2;
+};
+
+size_t sz_phi(const CDims& d) { return (size_t)d.rw * d.R * d.rv; }
+size_t sz_psi(const CDims& d) { return (size_t)d.rw2 * d.R2 * d.rv2; }
+size_t sz_u(const CDims& d) { return (size_t)d.rw * d.m * d.rw2; }
+size_t sz_op(const CDims& d) { return (size_t)d.R * d.m * d.n * d.R2; }
+size_t sz_v(const CDims& d) { return (size_t)d.rv * d.n * d.rv2; }
+
+void check_prec(int prec) {
+  TT_CHECK(prec == TT_FP64 || prec == TT_FP32 || prec == TT_MIXED_TF32 || prec == TT_MIXED_BF16,
+           TT_E_INVALID_ARG, "unknown precision");
+}
+
+}  // namespace
+
+void env_left_step(const CDims& d, const double* phi, const double* u, const double* op,
+                   const double* v, double* out, int prec, cudaStream_t st) {
+  check_prec(prec);
+  size_t t1n = (size_t)d.rw * d.R * d.n * d.rv2, t2n = (size_t)d.rw * d.m * d.R2 * d.rv2;
+  stats_begin(st);
+  if (prec == TT_FP64) {
+    DBuf<double> t1(t1n), t2(t2n);
+    env_left_t<double>(d, phi, u, op, v, out, t1.get(), t2.get(), st, prec);
+  } else {
+    F32Scratch s;
+    s.a.alloc(sz_phi(d)); s.b.alloc(sz_u(d)); s.c.alloc(sz_op(d)); s.d.alloc(sz_v(d));
+    s.e.alloc(sz_psi(d)); s.t1.alloc(t1n); s.t2.alloc(t2n);
+    to_float(phi, s.a.get(), sz_phi(d), st); to_float(u, s.b.get(), sz_u(d), st);
+    to_float(op, s.c.get(), sz_op(d), st); to_float(v, s.d.get(), sz_v(d), st);
+    env_left_t<float>(d, s.a.get(), s.b.get(), s.c.get(), s.d.get(), s.e.get(), s.t1.get(),
+                      s.t2.get(), st, prec);
+    to_double(s.e.get(), out, sz_psi(d), st);
+  }
+  stats_end(st, contract_flops(d));
+}
+
+void env_right_step(const CDims& d, const double* psi, const double* u, const double* op,
+                    const double* v, double* out, int prec, cudaStream_t st) {
+  check_prec(prec);
+  size_t t1n = (size_t)d.rv * d.n * d.rw2 * d.R2, t2n = (size_t)d.rv * d.R * d.m * d.rw2;
+  stats_begin(st);
+  if (prec == TT_FP64) {
+    DBuf<double> t1(t1n), t2(t2n);
+    env_right_t<double>(d, psi, u, op, v, out, t1.get(), t2.get(), st);
+  } else {
+    F32Scratch s;
+    s.a.alloc(sz_psi(d)); s.b.alloc(sz_u(d)); s.c.alloc(sz_op(d)); s.d.alloc(sz_v(d));
+    s.e.alloc(sz_phi(d)); s.t1.alloc(t1n); s.t2.alloc(t2n);
+    to_float(psi, s.a.get(), sz_psi(d), st); to_float(u, s.b.get(), sz_u(d), st);
+    to_float(op, s.c.get(), sz_op(d), st); to_float(v, s.d.get(), sz_v(d), st);
+    env_right_t<float>(d, s.a.get(), s.b.get(), s.c.get(), s.d.get(), s.e.get(), s.t1.get(),
+                       s.t2.get(), st);
+    to_double(s.e.get(), out, sz_phi(d), st);
+  }
+  stats_end(st, contract_flops(d));
+}
+
+void local_apply(const CDims& d, const double* phi, const double* op, const double* psi,
+                 const double* x, double* y, int prec, cudaStream_t st) {
+  check_prec(prec);
+  size_t t1n = (size_t)d.rw * d.R * d.n * d.rv2, t2n = (size_t)d.rw * d.m * d.R2 * d.rv2;
+  size_t yn = (size_t)d.rw * d.m * d.rw2;
+  stats_begin(st);
+  if (prec == TT_FP64) {
+    DBuf<double> t1(t1n), t2(t2n);
+    apply_t<double>(d, phi, op, psi, x, y, t1.get(), t2.get(), st, prec);
+  } else {
+    F32Scratch s;
+    s.a.alloc(sz_phi(d)); s.b.alloc(sz_psi(d)); s.c.alloc(sz_op(d)); s.d.alloc(sz_v(d));
+    s.e.alloc(yn); s.t1.alloc(t1n); s.t2.alloc(t2n);
+    to_float(phi, s.a.get(), sz_phi(d), st); to_float(psi, s.b.get(), sz_psi(d), st);
+    to_float(op, s.c.get(), sz_op(d), st); to_float(x, s.d.get(), sz_v(d), st);
+    apply_t<float>(d, s.a.get(), s.c.get(), s.b.get(), s.d.get(), s.e.get(), s.t1.get(),
+                   s.t2.get(), st, prec);
+    to_double(s.e.get(), y, yn, st);
+  }
+  stats_end(st, contract_flops(d));
+}
+
+void local_matrix(const CDims& d, const double* phi, const double* op, const double* psi,
+                  double* out, int prec, cudaStream_t st) {
+  check_prec(prec);
+  size_t t1n = (size_t)d.rw * d.rv * d.m * d.n * d.R2;
+  size_t on = (size_t)d.rw * d.m * d.rw2 * (size_t)d.rv * d.n * d.rv2;
+  if (prec == TT_FP64) {
+    DBuf<double> t1(t1n);
+    local_matrix_t<double>(d, phi, op, psi, out, t1.get(), st);
+  } else {
+    F32Scratch s;
+    s.a.alloc(sz_phi(d)); s.b.alloc(sz_psi(d)); s.c.alloc(sz_op(d));
+    s.e.alloc(on); s.t1.alloc(t1n);
+    to_float(phi, s.a.get(), sz_phi(d), st); to_float(psi, s.b.get(), sz_psi(d), st);
+    to_float(op, s.c.get(), sz_op(d), st);
+    local_matrix_t<float>(d, s.a.get(), s.c.get(), s.b.get(), s.e.get(), s.t1.get(), st);
+    to_double(s.e.get(), out, on, st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// statistics: one event pair per contraction, resolved lazily
+// ---------------------------------------------------------------------------
+
+namespace {
+struct Stats {
+  std::mutex mu;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  double flops = 0.0, seconds = 0.0;
+  bool enabled = true;
+  cudaEvent_t open = nullptr;
+};
+Stats& stats() {
+  static Stats s;
+  return s;
+}
+}  // namespace
+
+void stats_begin(cudaStream_t st) {
+  Stats& s = stats();
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (!s.enabled) return;
+  std::pair<cudaEvent_t, cudaEvent_t> ev;
+  if (!s.pool.empty()) {
+    ev = s.pool.back();
+    s.pool.pop_back();
+  } else {
+    TT_CUDA(cudaEventCreate(&ev.first));
+    TT_CUDA(cudaEventCreate(&ev.second));
+  }
+  TT_CUDA(cudaEventRecord(ev.first, st));
+  s.pending.push_back(ev);
+}
+
+void stats_end(cudaStream_t st, double flops) {
+  Stats& s = stats();
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (!s.enabled || s.pending.empty()) return;
+  TT_CUDA(cudaEventRecord(s.pending.back().second, st));
+  s.flops += flops;
+  if (s.pending.size() > 4096) {
+    // resolve older pairs to bound the pool
+    for (auto& ev : s.pending) {
+      TT_CUDA(cudaEventSynchronize(ev.second));
+      float ms = 0.f;
+      TT_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
+      s.seconds += ms * 1e-3;
+      s.pool.push_back(ev);
+    }
+    s.pending.clear();
+  }
+}
+
+void stats_read(double* flops, double* seconds) {
+  Stats& s = stats();
+  std::lock_guard<std::mutex> lk(s.mu);
+  for (auto& ev : s.pending) {
+    TT_CUDA(cudaEventSynchronize(ev.second));
+    float ms = 0.f;
+    TT_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
+    s.seconds += ms * 1e-3;
+    s.pool.push_back(ev);
+  }
+  s.pending.clear();
+  if (flops) *flops = s.flops;
+  if (seconds) *seconds = s.seconds;
+}
+
+void stats_reset() {
+  double f, t;
+  stats_read(&f, &t);
+  Stats& s = stats();
+  std::lock_guard<std::mutex> lk(s.mu);
+  s.flops = 0.0;
+  s.seconds = 0.0;
+}
+
+}  // namespace ttsdp

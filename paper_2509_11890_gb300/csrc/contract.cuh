@@ -1,0 +1,34 @@
+// Three-operand TT contractions of the block-AMEn solver (Section 3.3, the
+// matrix-free local products with cached environments): left / right
+// environment updates, the local product and the dense projected operator.
+#pragma once
+
+#include "common.cuh"
+
+namespace ttsdp {
+
+struct CDims {
+  int rw, rw2, R, R2, rv, rv2, m, n;
+};
+
+// Algorithmic flops of one environment update or local product
+// (three GEMM stages; 2 flops per multiply-add).
+double contract_flops(const CDims& d);
+
+// All pointers device, FP64 storage; `prec` is a tt_precision.
+void env_left_step(const CDims& d, const double* phi, const double* u, const double* op,
+                   const double* v, double* out, int prec, cudaStream_t st);
+void env_right_step(const CDims& d, const double* psi, const double* u, const double* op,
+                    const double* v, double* out, int prec, cudaStream_t st);
+void local_apply(const CDims& d, const double* phi, const double* op, const double* psi,
+                 const double* x, double* y, int prec, cudaStream_t st);
+void local_matrix(const CDims& d, const double* phi, const double* op, const double* psi,
+                  double* out, int prec, cudaStream_t st);
+
+// Contraction statistics (device time via CUDA events and algorithmic flops).
+void stats_begin(cudaStream_t st);
+void stats_end(cudaStream_t st, double flops);
+void stats_read(double* flops, double* seconds);
+void stats_reset();
+
+}  // namespace ttsdp

@@ -1,0 +1,488 @@
+// Dense factorisations for the small matrices of the TT solver.
+//
+// The matrices are small (unfoldings of TT cores, projected local systems),
+// so QR, SVD, Cholesky and the triangular kernels run in one CTA each with
+// warp-shuffle reductions and the matrix resident in L2; the LU of the larger
+// local systems is blocked so that its trailing updates use the multi-CTA
+// strided GEMM.
+#include <cfloat>
+
+#include "gemm.cuh"
+#include "linalg.cuh"
+
+namespace ttsdp {
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread receives the result.
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T s = T(0);
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T eps_of();
+template <>
+__device__ __forceinline__ double eps_of<double>() { return DBL_EPSILON; }
+template <>
+__device__ __forceinline__ float eps_of<float>() { return FLT_EPSILON; }
+
+// ---------------------------------------------------------------------------
+// Householder QR (LAPACK-style reflectors, beta = -sign(alpha) ||x||)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) qr_kernel(MatView<T> A, T* W, T* tau, T* Q, T* R) {
+  __shared__ T red[kWarps];
+  __shared__ T s_beta, s_tau, s_scale;
+  const int m = A.m, n = A.n, k = m < n ? m : n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (long long idx = tid; idx < (long long)m * n; idx += kThreads) {
+    int i = (int)(idx / n), j = (int)(idx % n);
+    W[idx] = A.p[i * A.rs + j * A.cs];
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    T loc = T(0);
+    for (int i = j + 1 + tid; i < m; i += kThreads) {
+      T x = W[(long long)i * n + j];
+      loc += x * x;
+    }
+    T sigma = block_sum(loc, red);
+    if (tid == 0) {
+      T alpha = W[(long long)j * n + j];
+      if (sigma == T(0)) {
+        s_tau = T(0);
+        s_beta = alpha;
+        s_scale = T(0);
+      } else {
+        T nrm = sqrt(alpha * alpha + sigma);
+        T beta = alpha <= T(0) ? nrm : -nrm;
+        s_tau = (beta - alpha) / beta;
+        s_scale = T(1) / (alpha - beta);
+        s_beta = beta;
+      }
+      tau[j] = s_tau;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < m; i += kThreads) W[(long long)i * n + j] *= s_scale;
+    __syncthreads();
+    if (tid == 0) W[(long long)j * n + j] = s_beta;
+    const T tj = s_tau;
+    if (tj != T(0)) {
+      for (int c = j + 1 + warp; c < n; c += kWarps) {
+        T dot = T(0);
+        for (int i = j + 1 + lane; i < m; i += 32) dot += W[(long long)i * n + j] * W[(long long)i * n + c];
+        dot = warp_sum(dot);
+        dot += W[(long long)j * n + c];
+        T f = tj * dot;
+        if (lane == 0) W[(long long)j * n + c] -= f;
+        for (int i = j + 1 + lane; i < m; i += 32) W[(long long)i * n + c] -= f * W[(long long)i * n + j];
+      }
+    }
+    __syncthreads();
+  }
+  for (long long idx = tid; idx < (long long)k * n; idx += kThreads) {
+    int i = (int)(idx / n), c = (int)(idx % n);
+    R[idx] = c >= i ? W[(long long)i * n + c] : T(0);
+  }
+  for (long long idx = tid; idx < (long long)m * k; idx += kThreads) {
+    int i = (int)(idx / k), c = (int)(idx % k);
+    Q[idx] = i == c ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    if (tj != T(0)) {
+      for (int c = j + warp; c < k; c += kWarps) {
+        T dot = T(0);
+        for (int i = j + 1 + lane; i < m; i += 32) dot += W[(long long)i * n + j] * Q[(long long)i * k + c];
+        dot = warp_sum(dot);
+        dot += Q[(long long)j * k + c];
+        T f = tj * dot;
+        if (lane == 0) Q[(long long)j * k + c] -= f;
+        for (int i = j + 1 + lane; i < m; i += 32) Q[(long long)i * k + c] -= f * W[(long long)i * n + j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi SVD on the columns of an m x n matrix (m >= n), columns
+// stored contiguously; round-robin ordering so each round's pairs are disjoint.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transposed, T* Wc, T* Vc,
+                                                       T* U, T* S, T* Vt, int* perm) {
+  __shared__ int s_rot;
+  // work on B = A (m x n, m >= n) or B = A^T when A is wide
+  const int m = transposed ? A.n : A.m;
+  const int n = transposed ? A.m : A.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (long long idx = tid; idx < (long long)m * n; idx += kThreads) {
+    int j = (int)(idx / m), i = (int)(idx % m);  // column j, row i of B
+    Wc[idx] = transposed ? A.p[j * A.rs + i * A.cs] : A.p[i * A.rs + j * A.cs];
+  }
+  for (long long idx = tid; idx < (long long)n * n; idx += kThreads) {
+    int j = (int)(idx / n), i = (int)(idx % n);
+    Vc[idx] = i == j ? T(1) : T(0);
+  }
+  __syncthreads();
+  const T tol = T(8) * eps_of<T>();
+  const int nn = n + (n & 1);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < nn - 1; ++r) {
+      for (int pi = warp; pi < nn / 2; pi += kWarps) {
+        int x = pi, y = nn - 1 - pi;
+        int p = x == 0 ? 0 : ((x - 1 + r) % (nn - 1)) + 1;
+        int q = ((y - 1 + r) % (nn - 1)) + 1;
+        if (p >= n || q >= n) continue;
+        T* wp = Wc + (long long)p * m;
+        T* wq = Wc + (long long)q * m;
+        T a = T(0), b = T(0), g = T(0);
+        for (int i = lane; i < m; i += 32) {
+          T u = wp[i], v = wq[i];
+          a += u * u;
+          b += v * v;
+          g += u * v;
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (g != T(0) && fabs(g) > tol * sqrt(a * b)) {
+          T zeta = (b - a) / (T(2) * g);
+          T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          T c = T(1) / sqrt(T(1) + t * t);
+          T s = c * t;
+          for (int i = lane; i < m; i += 32) {
+            T u = wp[i], v = wq[i];
+            wp[i] = c * u - s * v;
+            wq[i] = s * u + c * v;
+          }
+          T* vp = Vc + (long long)p * n;
+          T* vq = Vc + (long long)q * n;
+          for (int i = lane; i < n; i += 32) {
+            T u = vp[i], v = vq[i];
+            vp[i] = c * u - s * v;
+            vq[i] = s * u + c * v;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  // singular values (column norms) and a descending order
+  for (int j = warp; j < n; j += kWarps) {
+    T a = T(0);
+    for (int i = lane; i < m; i += 32) a += Wc[(long long)j * m + i] * Wc[(long long)j * m + i];
+    a = warp_sum(a);
+    if (lane == 0) S[j] = sqrt(a);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < n; ++j) perm[j] = j;
+    for (int j = 1; j < n; ++j) {  // insertion sort, stable
+      int pj = perm[j];
+      T v = S[pj];
+      int t = j - 1;
+      while (t >= 0 && S[perm[t]] < v) {
+        perm[t + 1] = perm[t];
+        --t;
+      }
+      perm[t + 1] = pj;
+    }
+  }
+  __syncthreads();
+  // B = Ub diag(S) Vb^T with Ub columns Wc/S, Vb = Vc (columns)
+  // A = B (not transposed): U = Ub (m x n), Vt = Vb^T (n x n)
+  // A = B^T (transposed):  A = Vb S Ub^T: U = Vb (A.m = n rows), Vt = Ub^T (n x m)
+  const int k = n;
+  for (long long idx = tid; idx < (long long)m * k; idx += kThreads) {
+    int i = (int)(idx / k), r = (int)(idx % k);
+    int c = perm[r];
+    T s = S[c];
+    T val = s > T(0) ? Wc[(long long)c * m + i] / s : T(0);
+    if (!transposed) U[(long long)i * k + r] = val;       // U (m x k)
+    else Vt[(long long)r * m + i] = val;                   // Vt (k x m)
+  }
+  for (long long idx = tid; idx < (long long)n * k; idx += kThreads) {
+    int j = (int)(idx / k), r = (int)(idx % k);
+    T val = Vc[(long long)perm[r] * n + j];
+    if (!transposed) Vt[(long long)r * n + j] = val;       // Vt (k x n)
+    else U[(long long)j * k + r] = val;                    // U (n x k) = A.m x k
+  }
+  __syncthreads();
+  // S in descending order (reuse Wc's first column as scratch is unsafe; do it serially)
+  if (tid == 0) {
+    for (int r = 0; r < k; ++r) Wc[r] = S[perm[r]];
+    for (int r = 0; r < k; ++r) S[r] = Wc[r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// blocked LU with partial pivoting on [A | b]
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) lu_panel_kernel(int n, T* A, T* b, int j0, int jb, int* ipiv) {
+  __shared__ T rv[kWarps];
+  __shared__ int ri[kWarps];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int jj = j0; jj < j0 + jb; ++jj) {
+    T best = T(-1);
+    int bi = jj;
+    for (int i = jj + tid; i < n; i += kThreads) {
+      T v = fabs(A[(long long)i * n + jj]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      T bv = rv[0];
+      int bidx = ri[0];
+      for (int w = 1; w < kWarps; ++w)
+        if (rv[w] > bv || (rv[w] == bv && ri[w] < bidx)) { bv = rv[w]; bidx = ri[w]; }
+      s_piv = bidx;
+      ipiv[jj] = bidx;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != jj) {
+      for (int c = j0 + tid; c < j0 + jb; c += kThreads) {
+        T t = A[(long long)jj * n + c];
+        A[(long long)jj * n + c] = A[(long long)piv * n + c];
+        A[(long long)piv * n + c] = t;
+      }
+    }
+    __syncthreads();
+    const T p = A[(long long)jj * n + jj];
+    const T inv = p != T(0) ? T(1) / p : T(0);
+    for (int i = jj + 1 + tid; i < n; i += kThreads) A[(long long)i * n + jj] *= inv;
+    __syncthreads();
+    const int ncol = j0 + jb - (jj + 1);
+    if (ncol > 0) {
+      long long tot = (long long)(n - jj - 1) * ncol;
+      for (long long e = tid; e < tot; e += kThreads) {
+        int i = jj + 1 + (int)(e / ncol), c = jj + 1 + (int)(e % ncol);
+        A[(long long)i * n + c] -= A[(long long)i * n + jj] * A[(long long)jj * n + c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void lu_swap_trsm_kernel(int n, T* A, T* b, int j0, int jb, const int* ipiv) {
+  // one thread per column outside the panel (and the right-hand side)
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int ncols = n - jb + 1;
+  if (c >= ncols) return;
+  int col = c < j0 ? c : c + jb;  // skip the panel columns; col == n means b
+  auto at = [&](int i) -> T& { return col < n ? A[(long long)i * n + col] : b[i]; };
+  for (int jj = j0; jj < j0 + jb; ++jj) {
+    int piv = ipiv[jj];
+    if (piv != jj) {
+      T t = at(jj);
+      at(jj) = at(piv);
+      at(piv) = t;
+    }
+  }
+  if (col >= j0 + jb) {
+    // unit lower triangular solve with the panel's L11
+    for (int r = 1; r < jb; ++r) {
+      T s = at(j0 + r);
+      for (int t = 0; t < r; ++t) s -= A[(long long)(j0 + r) * n + j0 + t] * at(j0 + t);
+      at(j0 + r) = s;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) upper_solve_kernel(int n, const T* A, T* b) {
+  __shared__ T s_x;
+  for (int i = n - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      T d = A[(long long)i * n + i];
+      s_x = d != T(0) ? b[i] / d : T(0);
+      b[i] = s_x;
+    }
+    __syncthreads();
+    T x = s_x;
+    for (int j = threadIdx.x; j < i; j += kThreads) b[j] -= A[(long long)j * n + i] * x;
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) cholesky_kernel(int n, T* A) {
+  __shared__ T s_d;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      T v = A[(long long)j * n + j];
+      s_d = v > T(0) ? sqrt(v) : T(0);
+      A[(long long)j * n + j] = s_d;
+    }
+    __syncthreads();
+    T d = s_d;
+    T inv = d > T(0) ? T(1) / d : T(0);
+    for (int i = j + 1 + threadIdx.x; i < n; i += kThreads) A[(long long)i * n + j] *= inv;
+    __syncthreads();
+    int rem = n - j - 1;
+    long long tot = (long long)rem * rem;
+    for (long long e = threadIdx.x; e < tot; e += kThreads) {
+      int i = j + 1 + (int)(e / rem), c = j + 1 + (int)(e % rem);
+      if (c <= i) A[(long long)i * n + c] -= A[(long long)i * n + j] * A[(long long)c * n + j];
+    }
+    __syncthreads();
+  }
+  for (long long e = threadIdx.x; e < (long long)n * n; e += kThreads) {
+    int i = (int)(e / n), c = (int)(e % n);
+    if (c > i) A[e] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) tri_inv_kernel(int n, const T* L, T* X) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j < n; j += kWarps) {
+    for (int i = lane; i < n; i += 32) X[(long long)i * n + j] = T(0);
+    __syncwarp();
+    if (lane == 0) X[(long long)j * n + j] = T(1) / L[(long long)j * n + j];
+    __syncwarp();
+    for (int i = j + 1; i < n; ++i) {
+      T s = T(0);
+      for (int t = j + lane; t < i; t += 32) s += L[(long long)i * n + t] * X[(long long)t * n + j];
+      s = warp_sum(s);
+      if (lane == 0) X[(long long)i * n + j] = -s / L[(long long)i * n + i];
+      __syncwarp();
+    }
+  }
+}
+
+template <typename T>
+__global__ void transpose_kernel(int m, int n, const T* in, T* out) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * n) return;
+  int i = (int)(idx / n), j = (int)(idx % n);
+  out[(long long)j * m + i] = in[idx];
+}
+
+}  // namespace
+
+template <typename T>
+void qr_thin(MatView<T> A, T* Q, T* R, cudaStream_t st) {
+  if (A.m == 0 || A.n == 0) return;
+  int k = A.m < A.n ? A.m : A.n;
+  DBuf<T> W((size_t)A.m * A.n), tau((size_t)k);
+  qr_kernel<T><<<1, kThreads, 0, st>>>(A, W.get(), tau.get(), Q, R);
+  count_launch();
+  check_launch("qr_kernel");
+}
+
+template <typename T>
+void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st) {
+  if (A.m == 0 || A.n == 0) return;
+  bool tr = A.m < A.n;
+  int m = tr ? A.n : A.m, n = tr ? A.m : A.n;
+  DBuf<T> Wc((size_t)m * n), Vc((size_t)n * n);
+  DBuf<int> perm((size_t)n);
+  svd_kernel<T><<<1, kThreads, 0, st>>>(A, tr, Wc.get(), Vc.get(), U, S, Vt, perm.get());
+  count_launch();
+  check_launch("svd_kernel");
+}
+
+template <typename T>
+void lu_solve(int n, T* A, T* b, cudaStream_t st) {
+  if (n <= 0) return;
+  constexpr int nb = 32;
+  DBuf<int> ipiv((size_t)n);
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    int jb = n - j0 < nb ? n - j0 : nb;
+    lu_panel_kernel<T><<<1, kThreads, 0, st>>>(n, A, b, j0, jb, ipiv.get());
+    count_launch();
+    int ncols = n - jb + 1;
+    lu_swap_trsm_kernel<T><<<ceil_div(ncols, 128), 128, 0, st>>>(n, A, b, j0, jb, ipiv.get());
+    count_launch();
+    int rest = n - j0 - jb;
+    if (rest > 0) {
+      // A22 -= A21 A12 ; b2 -= A21 b1
+      gemm_rm<T>(false, false, rest, rest, jb, T(-1), A + (long long)(j0 + jb) * n + j0, n, 0,
+                 A + (long long)j0 * n + j0 + jb, n, 0, T(1), A + (long long)(j0 + jb) * n + j0 + jb, n,
+                 0, 1, st);
+      gemm_rm<T>(false, false, rest, 1, jb, T(-1), A + (long long)(j0 + jb) * n + j0, n, 0, b + j0, 1,
+                 0, T(1), b + j0 + jb, 1, 0, 1, st);
+    }
+  }
+  check_launch("lu");
+  upper_solve_kernel<T><<<1, kThreads, 0, st>>>(n, A, b);
+  count_launch();
+  check_launch("upper_solve");
+}
+
+template <typename T>
+void cholesky_lower(int n, T* A, cudaStream_t st) {
+  if (n <= 0) return;
+  cholesky_kernel<T><<<1, kThreads, 0, st>>>(n, A);
+  count_launch();
+  check_launch("cholesky");
+}
+
+template <typename T>
+void tri_lower_inverse(int n, T* L, cudaStream_t st) {
+  if (n <= 0) return;
+  DBuf<T> X((size_t)n * n);
+  tri_inv_kernel<T><<<1, kThreads, 0, st>>>(n, L, X.get());
+  count_launch();
+  TT_CUDA(cudaMemcpyAsync(L, X.get(), sizeof(T) * n * n, cudaMemcpyDeviceToDevice, st));
+  check_launch("tri_inv");
+}
+
+template <typename T>
+void transpose(int m, int n, const T* in, T* out, cudaStream_t st) {
+  long long tot = (long long)m * n;
+  if (tot == 0) return;
+  transpose_kernel<T><<<ceil_div(tot, 256), 256, 0, st>>>(m, n, in, out);
+  count_launch();
+  check_launch("transpose");
+}
+
+#define INST(T)                                                                 \
+  template void qr_thin<T>(MatView<T>, T*, T*, cudaStream_t);                   \
+  template void svd_thin<T>(MatView<T>, T*, T*, T*, cudaStream_t);              \
+  template void lu_solve<T>(int, T*, T*, cudaStream_t);                         \
+  template void cholesky_lower<T>(int, T*, cudaStream_t);                       \
+  template void tri_lower_inverse<T>(int, T*, cudaStream_t);                    \
+  template void transpose<T>(int, int, const T*, T*, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace ttsdp

@@ -1,0 +1,44 @@
+// Small dense factorisations used by TT rounding, the AMEn block-index move,
+// the local solves and the step-length eigenproblems.
+#pragma once
+
+#include "common.cuh"
+
+namespace ttsdp {
+
+// Strided view of an m x n matrix: element (i, j) at p[i * rs + j * cs].
+template <typename T>
+struct MatView {
+  const T* p;
+  int m, n;
+  long long rs, cs;
+};
+
+// Thin Householder QR of A (m x n): Q (m x k) and R (k x n), k = min(m, n),
+// both written row-major and dense. Single CTA.
+template <typename T>
+void qr_thin(MatView<T> A, T* Q, T* R, cudaStream_t st);
+
+// Thin SVD A = U diag(S) Vt by one-sided Jacobi (Hestenes), k = min(m, n),
+// singular values descending; U (m x k), S (k), Vt (k x n) row-major.
+// Single CTA. Returns nothing; the sweep count is bounded (60).
+template <typename T>
+void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st);
+
+// Solves A x = b in place (A n x n row-major, destroyed; b n-vector becomes x)
+// by LU with partial pivoting, right-looking and blocked (panel width 32).
+template <typename T>
+void lu_solve(int n, T* A, T* b, cudaStream_t st);
+
+// Lower Cholesky factor in place (row-major n x n; upper part zeroed) and
+// the inverse of a lower triangular matrix in place. Single CTA.
+template <typename T>
+void cholesky_lower(int n, T* A, cudaStream_t st);
+template <typename T>
+void tri_lower_inverse(int n, T* L, cudaStream_t st);
+
+// y = x transposed copy: out (n x m) = in (m x n)^T, both row-major.
+template <typename T>
+void transpose(int m, int n, const T* in, T* out, cudaStream_t st);
+
+}  // namespace ttsdp

@@ -1,0 +1,866 @@
+// Block-AMEn Newton solves, ALS step lengths and the interior-point iteration.
+//
+// Environments of every (frame, operator, vector) triple are cached on the
+// device and updated core by core with the three-stage contractions; the
+// reduced projected system (eq. reduced_kkt_system) is assembled from the
+// dense local operators and solved by LU; the block index is moved by a
+// truncated SVD with a random kick; rounding uses the spectral shift of
+// Corollary psdness_rounding.
+#include <cmath>
+#include <limits>
+
+#include "contract.cuh"
+#include "gemm.cuh"
+#include "linalg.cuh"
+#include "solver.cuh"
+
+namespace ttsdp {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// environments of <W, Op V>
+// ---------------------------------------------------------------------------
+struct Env {
+  DTT op;
+  const DTT* vec = nullptr;  // null: the frame itself
+  std::vector<DBuf<double>> L, R;
+
+  Env(DTT o, const DTT* v, int d) : op(std::move(o)), vec(v), L(d + 1), R(d + 1) {
+    L[0].alloc(1);
+    R[d].alloc(1);
+    dev_fill(L[0].get(), 1, 1.0, cur_stream());
+    dev_fill(R[d].get(), 1, 1.0, cur_stream());
+  }
+  const DTT& V(const DTT& frame) const { return vec ? *vec : frame; }
+  CDims dims(const DTT& frame, int k) const {
+    const DTT& v = V(frame);
+    return CDims{frame.r[k], frame.r[k + 1], op.r[k], op.r[k + 1], v.r[k], v.r[k + 1], op.m, op.n};
+  }
+  void push_left(const DTT& frame, int k, int prec) {
+    CDims c = dims(frame, k);
+    L[k + 1].alloc((size_t)c.rw2 * c.R2 * c.rv2);
+    env_left_step(c, L[k].get(), frame.core(k), op.core(k), V(frame).core(k), L[k + 1].get(), prec,
+                  cur_stream());
+  }
+  void push_right(const DTT& frame, int k, int prec) {
+    CDims c = dims(frame, k);
+    R[k].alloc((size_t)c.rw * c.R * c.rv);
+    env_right_step(c, R[k + 1].get(), frame.core(k), op.core(k), V(frame).core(k), R[k].get(), prec,
+                   cur_stream());
+  }
+  // W_{!=k}^T Op vec(V) at core k, written to y (rw * m * rw2)
+  void local_rhs(const DTT& frame, int k, double* y, int prec) const {
+    CDims c = dims(frame, k);
+    local_apply(c, L[k].get(), op.core(k), R[k + 1].get(), vec->core(k), y, prec, cur_stream());
+  }
+  void local_mat(const DTT& frame, int k, double* out, int prec) const {
+    CDims c{frame.r[k], frame.r[k + 1], op.r[k], op.r[k + 1], frame.r[k], frame.r[k + 1], op.m, op.n};
+    local_matrix(c, L[k].get(), op.core(k), R[k + 1].get(), out, prec, cur_stream());
+  }
+};
+
+struct RhsTerm {
+  double coef;
+  DTT op;
+  DTT vec;
+};
+
+struct NewtonData {
+  DTT A, AT, K;
+  std::vector<DTT> LZ, LX;
+  std::vector<RhsTerm> rp, rd, rc, rt;
+  bool ineq = false;
+  DTT TA, AiT;
+  std::vector<DTT> DK;
+  double sgn = 1.0;
+  int nblk() const { return ineq ? 4 : 3; }
+};
+
+DTT op_kron_left(const DTT& m) { return tt_kron(m, tt_identity(m.d, 2)); }   // M kron I: vec(M X)
+DTT op_kron_right(const DTT& m) { return tt_kron(tt_identity(m.d, 2), m); }  // I kron M: vec(X M^T)
+DTT vecv(const DTT& m) { return m.view(m.m * m.n, 1); }
+DTT unvec(const DTT& v) { return v.view(2, 2); }
+
+void sum_local_mats(std::vector<Env>& es, const DTT& frame, int k, double* out, size_t n, int prec) {
+  dev_fill(out, n * n, 0.0, cur_stream());
+  DBuf<double> tmp(n * n);
+  for (Env& e : es) {
+    e.local_mat(frame, k, tmp.get(), prec);
+    dev_axpy(out, tmp.get(), n * n, 1.0, cur_stream());
+  }
+}
+
+void sum_local_rhs(std::vector<std::pair<double, Env>>& es, const DTT& frame, int k, double* out, size_t n,
+                   int prec) {
+  dev_fill(out, n, 0.0, cur_stream());
+  DBuf<double> tmp(n);
+  for (auto& pe : es) {
+    if (pe.first == 0.0) continue;
+    pe.second.local_rhs(frame, k, tmp.get(), prec);
+    dev_axpy(out, tmp.get(), n, pe.first, cur_stream());
+  }
+}
+
+double dev_norm(const double* p, size_t n) { return std::sqrt(std::max(0.0, dev_dot(p, p, n, cur_stream()))); }
+
+std::vector<double> host_copy(const double* p, size_t n) {
+  std::vector<double> h(n);
+  TT_CUDA(cudaMemcpyAsync(h.data(), p, n * sizeof(double), cudaMemcpyDeviceToHost, cur_stream()));
+  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  return h;
+}
+
+void upload(double* dst, const std::vector<double>& h) {
+  TT_CUDA(cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, cur_stream()));
+  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+}
+
+int truncation_rank_rel(const std::vector<double>& s, double tol_rel, int cap) {
+  double nrm2 = 0.0;
+  for (double v : s) nrm2 += v * v;
+  return truncation_rank(s, tol_rel * std::sqrt(nrm2), cap);
+}
+
+// ---------------------------------------------------------------------------
+// block-AMEn
+// ---------------------------------------------------------------------------
+BlockTT init_block(int d, int nblk, int rk, Counter& rnd) {
+  std::vector<int> r(d + 1, 1);
+  for (int k = 1; k < d; ++k) {
+    long long cap = 1;
+    int e = std::min(k, d - k);
+    for (int t = 0; t < e && cap < rk; ++t) cap *= 4;
+    r[k] = (int)std::min<long long>(rk, cap);
+  }
+  DTT c = tt_alloc(d, r, 4, 1);
+  for (int k = 0; k < d; ++k) upload(c.core(k), rnd.draw(c.csize(k)));
+  BlockTT w;
+  w.frame = tt_orth_right(c);
+  w.nblk = nblk;
+  size_t n0 = w.frame.csize(0);
+  w.block = std::make_shared<DBuf<double>>(nblk * n0);
+  dev_fill(w.block->get(), nblk * n0, 0.0, cur_stream());
+  return w;
+}
+
+struct AmenInfo {
+  int sweeps = 0;
+  double max_change = 0.0;
+};
+
+BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap, int kick, int max_sweeps,
+                   Counter& rnd, int prec, AmenInfo* info) {
+  const int nblk = nd.nblk();
+  cudaStream_t st = cur_stream();
+  BlockTT w = w0 ? *w0 : init_block(d, nblk, kick, rnd);
+  DTT frame = w.frame;  // shares cores; replaced core by core below
+  frame.c = w.frame.c;
+  std::shared_ptr<DBuf<double>> block = w.block;
+  // environments
+  std::vector<Env> eA, eAT, eK, eLZ, eLX, eTA, eAiT, eDK;
+  eA.emplace_back(nd.A, nullptr, d);
+  eAT.emplace_back(nd.AT, nullptr, d);
+  eK.emplace_back(nd.K, nullptr, d);
+  for (auto& o : nd.LZ) eLZ.emplace_back(o, nullptr, d);
+  for (auto& o : nd.LX) eLX.emplace_back(o, nullptr, d);
+  std::vector<std::pair<double, Env>> rp, rdd, rc, rt;
+  for (auto& t : nd.rp) rp.emplace_back(t.coef, Env(t.op, &t.vec, d));
+  for (auto& t : nd.rd) rdd.emplace_back(t.coef, Env(t.op, &t.vec, d));
+  for (auto& t : nd.rc) rc.emplace_back(t.coef, Env(t.op, &t.vec, d));
+  if (nd.ineq) {
+    eTA.emplace_back(nd.TA, nullptr, d);
+    eAiT.emplace_back(nd.AiT, nullptr, d);
+    for (auto& o : nd.DK) eDK.emplace_back(o, nullptr, d);
+    for (auto& t : nd.rt) rt.emplace_back(t.coef, Env(t.op, &t.vec, d));
+  }
+  auto for_all = [&](auto fn) {
+    for (auto* v : {&eA, &eAT, &eK, &eLZ, &eLX, &eTA, &eAiT, &eDK})
+      for (Env& e : *v) fn(e);
+    for (auto* v : {&rp, &rdd, &rc, &rt})
+      for (auto& pe : *v) fn(pe.second);
+  };
+  for (int k = d - 1; k >= 1; --k) for_all([&](Env& e) { e.push_right(frame, k, prec); });
+
+  std::vector<int> blockshape = {frame.r[0], 4, frame.r[1]};
+  int sweep = 0;
+  double max_change = 0.0;
+  for (sweep = 0; sweep < max_sweeps; ++sweep) {
+    const bool forward = sweep % 2 == 0;
+    max_change = 0.0;
+    for (int step = 0; step < d; ++step) {
+      const int k = forward ? step : d - 1 - step;
+      const int rl = frame.r[k], rr = frame.r[k + 1];
+      const size_t n = (size_t)rl * 4 * rr;
+      const int nb = nd.ineq ? 3 : 2;
+      const size_t N = nb * n;
+      // local operators
+      DBuf<double> A(n * n), AT(n * n), Ky(n * n), LZ(n * n), LX(n * n);
+      eA[0].local_mat(frame, k, A.get(), prec);
+      eAT[0].local_mat(frame, k, AT.get(), prec);
+      eK[0].local_mat(frame, k, Ky.get(), prec);
+      sum_local_mats(eLZ, frame, k, LZ.get(), n, prec);
+      sum_local_mats(eLX, frame, k, LX.get(), n, prec);
+      DBuf<double> r_p(n), r_d(n), r_c(n);
+      sum_local_rhs(rp, frame, k, r_p.get(), n, prec);
+      sum_local_rhs(rdd, frame, k, r_d.get(), n, prec);
+      sum_local_rhs(rc, frame, k, r_c.get(), n, prec);
+      DBuf<double> K(N * N), b(N);
+      dev_fill(K.get(), N * N, 0.0, st);
+      // row block p: [-A, Ky, 0]
+      dev_copy2d(K.get(), N, A.get(), n, n, n, -1.0, st);
+      dev_copy2d(K.get() + n, N, Ky.get(), n, n, n, 1.0, st);
+      // last row block c: [LZ, LX AT, -sgn LX AiT]
+      const size_t rc0 = (nb - 1) * n;
+      dev_copy2d(K.get() + rc0 * N, N, LZ.get(), n, n, n, 1.0, st);
+      gemm_rm<double>(false, false, n, n, n, 1.0, LX.get(), n, 0, AT.get(), n, 0, 0.0, K.get() + rc0 * N + n,
+                      N, 0, 1, st);
+      // right-hand sides
+      dev_copy2d(b.get(), 1, r_p.get(), 1, n, 1, -1.0, st);
+      dev_copy2d(b.get() + rc0, 1, r_c.get(), 1, n, 1, -1.0, st);
+      gemm_rm<double>(false, false, n, 1, n, 1.0, LX.get(), n, 0, r_d.get(), 1, 0, 1.0, b.get() + rc0, 1, 0,
+                      1, st);
+      DBuf<double> AiT;
+      if (nd.ineq) {
+        DBuf<double> TA(n * n), DK(n * n), r_t(n);
+        AiT.alloc(n * n);
+        eTA[0].local_mat(frame, k, TA.get(), prec);
+        eAiT[0].local_mat(frame, k, AiT.get(), prec);
+        sum_local_mats(eDK, frame, k, DK.get(), n, prec);
+        sum_local_rhs(rt, frame, k, r_t.get(), n, prec);
+        // row block t: [sgn TA, 0, DK]
+        dev_copy2d(K.get() + n * N, N, TA.get(), n, n, n, nd.sgn, st);
+        dev_copy2d(K.get() + n * N + 2 * n, N, DK.get(), n, n, n, 1.0, st);
+        gemm_rm<double>(false, false, n, n, n, -nd.sgn, LX.get(), n, 0, AiT.get(), n, 0, 0.0,
+                        K.get() + rc0 * N + 2 * n, N, 0, 1, st);
+        dev_copy2d(b.get() + n, 1, r_t.get(), 1, n, 1, -1.0, st);
+      }
+      lu_solve<double>((int)N, K.get(), b.get(), st);
+      // assemble the new block core [dX, dY, (dT), dZ]
+      auto nw = std::make_shared<DBuf<double>>(nblk * n);
+      dev_copy(nw->get(), b.get(), nb * n, st);
+      double* dZ = nw->get() + (nblk - 1) * n;
+      // dZ = AT dY - sgn AiT dT - r_d
+      gemm_rm<double>(false, false, n, 1, n, 1.0, AT.get(), n, 0, b.get() + n, 1, 0, 0.0, dZ, 1, 0, 1, st);
+      if (nd.ineq)
+        gemm_rm<double>(false, false, n, 1, n, -nd.sgn, AiT.get(), n, 0, b.get() + 2 * n, 1, 0, 1.0, dZ, 1, 0,
+                        1, st);
+      dev_axpy(dZ, r_d.get(), n, -1.0, st);
+      // convergence measure
+      double nrm = dev_norm(nw->get(), nblk * n);
+      if (blockshape[0] == rl && blockshape[2] == rr && block) {
+        DBuf<double> diff(nblk * n);
+        dev_copy(diff.get(), nw->get(), nblk * n, st);
+        dev_axpy(diff.get(), block->get(), nblk * n, -1.0, st);
+        max_change = std::max(max_change, dev_norm(diff.get(), nblk * n) / std::max(nrm, 1e-300));
+      } else {
+        max_change = std::max(max_change, 1.0);
+      }
+      const bool last = forward ? (k == d - 1) : (k == 0);
+      if (last) {
+        block = nw;
+        blockshape = {rl, 4, rr};
+        auto c0 = std::make_shared<DBuf<double>>(n);
+        dev_copy(c0->get(), nw->get(), n, st);
+        frame.c[k] = c0;
+        break;
+      }
+      if (forward) {
+        const int rows = rl * 4, cols = nblk * rr;
+        DBuf<double> mat((size_t)rows * cols);
+        for (int bb = 0; bb < nblk; ++bb)
+          dev_copy2d(mat.get() + bb * rr, cols, nw->get() + bb * n, rr, rows, rr, 1.0, st);
+        int kk = std::min(rows, cols);
+        DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
+        svd_thin<double>(MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+        std::vector<double> hs = host_copy(S.get(), kk);
+        int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
+        int extra = std::min(kick, std::min(rows - keep, std::max(cap - keep, 0)));
+        int nk = keep + std::max(extra, 0);
+        DBuf<double> u((size_t)rows * nk);
+        dev_copy2d(u.get(), nk, U.get(), kk, rows, keep, 1.0, st);
+        if (extra > 0) {
+          std::vector<double> rndv = rnd.draw((size_t)rows * extra);
+          DBuf<double> rr_((size_t)rows * extra);
+          upload(rr_.get(), rndv);
+          dev_copy2d(u.get() + keep, nk, rr_.get(), extra, rows, extra, 1.0, st);
+          DBuf<double> Q((size_t)rows * nk), Rq((size_t)nk * nk);
+          qr_thin<double>(MatView<double>{u.get(), rows, nk, nk, 1}, Q.get(), Rq.get(), st);
+          dev_copy(u.get(), Q.get(), (size_t)rows * nk, st);
+        }
+        DBuf<double> coef((size_t)nk * cols);
+        gemm_rm<double>(true, false, nk, cols, rows, 1.0, u.get(), nk, 0, mat.get(), cols, 0, 0.0, coef.get(),
+                        cols, 0, 1, st);
+        auto fk = std::make_shared<DBuf<double>>((size_t)rows * nk);
+        dev_copy(fk->get(), u.get(), (size_t)rows * nk, st);
+        frame.c[k] = fk;
+        frame.r[k + 1] = nk;
+        const int r3 = frame.r[k + 2];
+        const size_t nn = (size_t)nk * 4 * r3;
+        auto nb2 = std::make_shared<DBuf<double>>(nblk * nn);
+        for (int bb = 0; bb < nblk; ++bb)
+          gemm_rm<double>(false, false, nk, 4 * r3, rr, 1.0, coef.get() + bb * rr, cols, 0, frame.core(k + 1),
+                          4 * r3, 0, 0.0, nb2->get() + bb * nn, 4 * r3, 0, 1, st);
+        auto c1 = std::make_shared<DBuf<double>>(nn);
+        dev_copy(c1->get(), nb2->get(), nn, st);
+        frame.c[k + 1] = c1;
+        block = nb2;
+        blockshape = {nk, 4, r3};
+        for_all([&](Env& e) { e.push_left(frame, k, prec); });
+      } else {
+        const int rows = nblk * rl, cols = 4 * rr;
+        int kk = std::min(rows, cols);
+        DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
+        svd_thin<double>(MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+        std::vector<double> hs = host_copy(S.get(), kk);
+        int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
+        int extra = std::min(kick, std::min(cols - keep, std::max(cap - keep, 0)));
+        int nk = keep + std::max(extra, 0);
+        DBuf<double> v((size_t)cols * nk);  // cols x nk
+        DBuf<double> vt_keep((size_t)keep * cols);
+        dev_copy(vt_keep.get(), Vt.get(), (size_t)keep * cols, st);
+        DBuf<double> vk((size_t)cols * keep);
+        transpose<double>(keep, cols, vt_keep.get(), vk.get(), st);
+        dev_copy2d(v.get(), nk, vk.get(), keep, cols, keep, 1.0, st);
+        if (extra > 0) {
+          std::vector<double> rndv = rnd.draw((size_t)cols * extra);
+          DBuf<double> rr_((size_t)cols * extra);
+          upload(rr_.get(), rndv);
+          dev_copy2d(v.get() + keep, nk, rr_.get(), extra, cols, extra, 1.0, st);
+          DBuf<double> Q((size_t)cols * nk), Rq((size_t)nk * nk);
+          qr_thin<double>(MatView<double>{v.get(), cols, nk, nk, 1}, Q.get(), Rq.get(), st);
+          dev_copy(v.get(), Q.get(), (size_t)cols * nk, st);
+        }
+        DBuf<double> coef((size_t)rows * nk);  // (nblk rl) x nk
+        gemm_rm<double>(false, false, rows, nk, cols, 1.0, nw->get(), cols, 0, v.get(), nk, 0, 0.0, coef.get(),
+                        nk, 0, 1, st);
+        auto fk = std::make_shared<DBuf<double>>((size_t)nk * cols);
+        transpose<double>(cols, nk, v.get(), fk->get(), st);
+        frame.c[k] = fk;
+        frame.r[k] = nk;
+        const int rp = frame.r[k - 1];
+        const size_t nn = (size_t)rp * 4 * nk;
+        auto nb2 = std::make_shared<DBuf<double>>(nblk * nn);
+        for (int bb = 0; bb < nblk; ++bb)
+          gemm_rm<double>(false, false, rp * 4, nk, rl, 1.0, frame.core(k - 1), rl, 0,
+                          coef.get() + (size_t)bb * rl * nk, nk, 0, 0.0, nb2->get() + bb * nn, nk, 0, 1, st);
+        auto c1 = std::make_shared<DBuf<double>>(nn);
+        dev_copy(c1->get(), nb2->get(), nn, st);
+        frame.c[k - 1] = c1;
+        block = nb2;
+        blockshape = {rp, 4, nk};
+        for_all([&](Env& e) { e.push_right(frame, k, prec); });
+      }
+    }
+    if (sweep >= 1 && max_change < tol) {
+      ++sweep;
+      break;
+    }
+  }
+  if (sweep > max_sweeps) sweep = max_sweeps;
+  info->sweeps = sweep;
+  info->max_change = max_change;
+  // bring the block index back to core 0 without truncation
+  const bool at_end = (sweep % 2 == 1);
+  if (at_end) {
+    for (int k = d - 1; k >= 1; --k) {
+      int rl = frame.r[k], rr = frame.r[k + 1];
+      int rows = nblk * rl, cols = 4 * rr;
+      int kk = std::min(rows, cols);
+      // QR of mat^T (cols x rows)
+      DBuf<double> Q((size_t)cols * kk), R((size_t)kk * rows);
+      qr_thin<double>(MatView<double>{block->get(), cols, rows, 1, cols}, Q.get(), R.get(), st);
+      auto fk = std::make_shared<DBuf<double>>((size_t)kk * cols);
+      transpose<double>(cols, kk, Q.get(), fk->get(), st);
+      frame.c[k] = fk;
+      frame.r[k] = kk;
+      // coef[b][a][c] = R^T[(b a)][c] ; new block[b] = frame[k-1] coef[b]
+      DBuf<double> RT((size_t)rows * kk);
+      transpose<double>(kk, rows, R.get(), RT.get(), st);
+      int rp = frame.r[k - 1];
+      size_t nn = (size_t)rp * 4 * kk;
+      auto nb2 = std::make_shared<DBuf<double>>(nblk * nn);
+      for (int bb = 0; bb < nblk; ++bb)
+        gemm_rm<double>(false, false, rp * 4, kk, rl, 1.0, frame.core(k - 1), rl, 0, RT.get() + (size_t)bb * rl * kk,
+                        kk, 0, 0.0, nb2->get() + bb * nn, kk, 0, 1, st);
+      auto c1 = std::make_shared<DBuf<double>>(nn);
+      dev_copy(c1->get(), nb2->get(), nn, st);
+      frame.c[k - 1] = c1;
+      block = nb2;
+    }
+  }
+  BlockTT out;
+  out.frame = frame;
+  out.nblk = nblk;
+  out.block = block;
+  return out;
+}
+
+}  // namespace
+
+DTT BlockTT::component(int b) const {
+  DTT t = frame;
+  size_t n0 = frame.csize(0);
+  auto c0 = std::make_shared<DBuf<double>>(n0);
+  dev_copy(c0->get(), block->get() + b * n0, n0, cur_stream());
+  t.c[0] = c0;
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// step length: alternating local generalised eigenproblems (Section 3.4)
+// ---------------------------------------------------------------------------
+static double local_min_eig(int nl, const double* Mk, const double* Dk, double* x) {
+  cudaStream_t st = cur_stream();
+  size_t nn = (size_t)nl * nl;
+  DBuf<double> L(nn), Ms(nn), Ds(nn), tmp(nn), S(nn);
+  // symmetrise
+  transpose<double>(nl, nl, Mk, tmp.get(), st);
+  dev_copy(Ms.get(), Mk, nn, st);
+  dev_axpy(Ms.get(), tmp.get(), nn, 1.0, st);
+  dev_scale(Ms.get(), nn, 0.5, st);
+  transpose<double>(nl, nl, Dk, tmp.get(), st);
+  dev_copy(Ds.get(), Dk, nn, st);
+  dev_axpy(Ds.get(), tmp.get(), nn, 1.0, st);
+  dev_scale(Ds.get(), nn, 0.5, st);
+  dev_copy(L.get(), Ms.get(), nn, st);
+  cholesky_lower<double>(nl, L.get(), st);
+  tri_lower_inverse<double>(nl, L.get(), st);  // L <- L^{-1}
+  // S = Li Ds Li^T
+  gemm_rm<double>(false, false, nl, nl, nl, 1.0, L.get(), nl, 0, Ds.get(), nl, 0, 0.0, tmp.get(), nl, 0, 1, st);
+  gemm_rm<double>(false, true, nl, nl, nl, 1.0, tmp.get(), nl, 0, L.get(), nl, 0, 0.0, S.get(), nl, 0, 1, st);
+  transpose<double>(nl, nl, S.get(), tmp.get(), st);
+  dev_axpy(S.get(), tmp.get(), nn, 1.0, st);
+  dev_scale(S.get(), nn, 0.5, st);
+  // smallest eigenpair of the symmetric S through the SVD of S + s I (s >= ||S||_F)
+  double s = dev_norm(S.get(), nn) + 1e-300;
+  std::vector<double> diag(nn, 0.0);
+  for (int i = 0; i < nl; ++i) diag[(size_t)i * nl + i] = s;
+  DBuf<double> dI(nn);
+  upload(dI.get(), diag);
+  dev_axpy(S.get(), dI.get(), nn, 1.0, st);
+  DBuf<double> U(nn), Sv(nl), Vt(nn);
+  svd_thin<double>(MatView<double>{S.get(), nl, nl, nl, 1}, U.get(), Sv.get(), Vt.get(), st);
+  std::vector<double> hs = host_copy(Sv.get(), nl);
+  double lam = hs[nl - 1] - s;
+  // v = last column of U; x = Li^T v
+  DBuf<double> v(nl);
+  dev_copy2d(v.get(), 1, U.get() + (nl - 1), nl, nl, 1, 1.0, st);
+  gemm_rm<double>(true, false, nl, 1, nl, 1.0, L.get(), nl, 0, v.get(), 1, 0, 0.0, x, 1, 0, 1, st);
+  return lam;
+}
+
+double min_gen_eig(const DTT& M, const DTT& dM, DTT* e_io, bool warm, Counter& rnd, int rank, int sweeps,
+                   int prec) {
+  const int d = M.d, nmode = M.m;
+  cudaStream_t st = cur_stream();
+  DTT e;
+  if (!warm) {
+    std::vector<int> r(d + 1, 1);
+    for (int k = 1; k < d; ++k) {
+      long long cap = 1;
+      int ex = std::min(k, d - k);
+      for (int t = 0; t < ex && cap < rank; ++t) cap *= nmode;
+      r[k] = (int)std::min<long long>(rank, cap);
+    }
+    e = tt_alloc(d, r, nmode, 1);
+    for (int k = 0; k < d; ++k) upload(e.core(k), rnd.draw(e.csize(k)));
+  } else {
+    e = tt_copy(*e_io);
+  }
+  e = tt_orth_right(e);
+  Env eM(M, nullptr, d), eD(dM, nullptr, d);
+  for (int k = d - 1; k >= 1; --k) {
+    eM.push_right(e, k, prec);
+    eD.push_right(e, k, prec);
+  }
+  double lam = std::numeric_limits<double>::infinity();
+  for (int sw = 0; sw < sweeps; ++sw) {
+    const bool forward = sw % 2 == 0;
+    for (int step = 0; step < d; ++step) {
+      const int k = forward ? step : d - 1 - step;
+      const int rl = e.r[k], rr = e.r[k + 1];
+      const int nl = rl * nmode * rr;
+      DBuf<double> Mk((size_t)nl * nl), Dk((size_t)nl * nl), x(nl);
+      eM.local_mat(e, k, Mk.get(), prec);
+      eD.local_mat(e, k, Dk.get(), prec);
+      lam = local_min_eig(nl, Mk.get(), Dk.get(), x.get());
+      const bool last = forward ? (k == d - 1) : (k == 0);
+      if (last) {
+        auto c = std::make_shared<DBuf<double>>(nl);
+        dev_copy(c->get(), x.get(), nl, st);
+        e.c[k] = c;
+        break;
+      }
+      if (forward) {
+        int rows = rl * nmode;
+        int extra = rank > 1 ? std::max(0, std::min(rank, rows) - 1) : 0;
+        int cols = rr + extra;
+        DBuf<double> mat((size_t)rows * cols);
+        dev_copy2d(mat.get(), cols, x.get(), rr, rows, rr, 1.0, st);
+        if (extra > 0) {
+          DBuf<double> rr_((size_t)rows * extra);
+          upload(rr_.get(), rnd.draw((size_t)rows * extra));
+          dev_copy2d(mat.get() + rr, cols, rr_.get(), extra, rows, extra, 1.0, st);
+        }
+        int kq = std::min(rows, cols);
+        DBuf<double> Q((size_t)rows * kq), R((size_t)kq * cols);
+        if (cols == rr && rank <= 1) {
+          qr_thin<double>(MatView<double>{mat.get(), rows, cols, cols, 1}, Q.get(), R.get(), st);
+        } else {
+          qr_thin<double>(MatView<double>{mat.get(), rows, cols, cols, 1}, Q.get(), R.get(), st);
+        }
+        int keep = std::min(kq, rank);
+        auto fk = std::make_shared<DBuf<double>>((size_t)rows * keep);
+        dev_copy2d(fk->get(), keep, Q.get(), kq, rows, keep, 1.0, st);
+        // coef = q^T x_mat (keep x rr); next core = coef core_{k+1}
+        DBuf<double> coef((size_t)keep * rr);
+        gemm_rm<double>(true, false, keep, rr, rows, 1.0, fk->get(), keep, 0, x.get(), rr, 0, 0.0, coef.get(), rr,
+                        0, 1, st);
+        int r3 = e.r[k + 2];
+        auto nx = std::make_shared<DBuf<double>>((size_t)keep * nmode * r3);
+        gemm_rm<double>(false, false, keep, nmode * r3, rr, 1.0, coef.get(), rr, 0, e.core(k + 1), nmode * r3, 0,
+                        0.0, nx->get(), nmode * r3, 0, 1, st);
+        e.c[k] = fk;
+        e.c[k + 1] = nx;
+        e.r[k + 1] = keep;
+        eM.push_left(e, k, prec);
+        eD.push_left(e, k, prec);
+      } else {
+        int cols0 = nmode * rr;
+        int extra = rank > 1 ? std::max(0, std::min(rank, cols0) - 1) : 0;
+        int ccount = rl + extra;
+        // matT = x^T ((nmode rr) x rl) with random columns appended
+        DBuf<double> matT((size_t)cols0 * ccount);
+        DBuf<double> xt((size_t)cols0 * rl);
+        transpose<double>(rl, cols0, x.get(), xt.get(), st);
+        dev_copy2d(matT.get(), ccount, xt.get(), rl, cols0, rl, 1.0, st);
+        if (extra > 0) {
+          DBuf<double> rr_((size_t)cols0 * extra);
+          upload(rr_.get(), rnd.draw((size_t)cols0 * extra));
+          dev_copy2d(matT.get() + rl, ccount, rr_.get(), extra, cols0, extra, 1.0, st);
+        }
+        int kq = std::min(cols0, ccount);
+        DBuf<double> Q((size_t)cols0 * kq), R((size_t)kq * ccount);
+        qr_thin<double>(MatView<double>{matT.get(), cols0, ccount, ccount, 1}, Q.get(), R.get(), st);
+        int keep = std::min(kq, rank);
+        DBuf<double> q((size_t)cols0 * keep);
+        dev_copy2d(q.get(), keep, Q.get(), kq, cols0, keep, 1.0, st);
+        auto fk = std::make_shared<DBuf<double>>((size_t)keep * cols0);
+        transpose<double>(cols0, keep, q.get(), fk->get(), st);
+        // coef = x_mat q (rl x keep); prev core = core_{k-1} coef
+        DBuf<double> coef((size_t)rl * keep);
+        gemm_rm<double>(false, false, rl, keep, cols0, 1.0, x.get(), cols0, 0, q.get(), keep, 0, 0.0, coef.get(),
+                        keep, 0, 1, st);
+        int rp = e.r[k - 1];
+        auto px = std::make_shared<DBuf<double>>((size_t)rp * nmode * keep);
+        gemm_rm<double>(false, false, rp * nmode, keep, rl, 1.0, e.core(k - 1), rl, 0, coef.get(), keep, 0, 0.0,
+                        px->get(), keep, 0, 1, st);
+        e.c[k] = fk;
+        e.c[k - 1] = px;
+        e.r[k] = keep;
+        eM.push_right(e, k, prec);
+        eD.push_right(e, k, prec);
+      }
+    }
+  }
+  if (e_io) *e_io = tt_orth_right(e);
+  return lam;
+}
+
+static double step_from_lambda(double lam) {
+  return lam >= 0 ? std::numeric_limits<double>::infinity() : -1.0 / lam;
+}
+
+// ---------------------------------------------------------------------------
+// problem assembly (Section 4)
+// ---------------------------------------------------------------------------
+static DTT ones_vec(int d) {
+  DTT t = tt_alloc(d, std::vector<int>(d + 1, 1), 2, 1);
+  for (int k = 0; k < d; ++k) dev_fill(t.core(k), 2, 1.0, cur_stream());
+  return t;
+}
+
+static DTT unit_first(int d) {
+  DTT t = tt_alloc(d, std::vector<int>(d + 1, 1), 2, 2);
+  std::vector<double> h = {1.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < d; ++k) upload(t.core(k), h);
+  return t;
+}
+
+Problem build_maxcut(const DTT& w) {
+  const int d = w.d;
+  Problem p;
+  p.d = d;
+  DTT deg = tt_matvec(w, ones_vec(d));  // A_G 1, mode 2
+  p.C = tt_add(tt_diag(deg), w, 0.25, -0.25);
+  DTT I = tt_identity(d, 2), J = tt_ones_mat(d, 2);
+  p.A_eq = tt_diag(vecv(I));
+  p.B_eq = vecv(tt_copy(I));
+  p.K_y = tt_diag(vecv(tt_add(J, I, 1.0, -1.0)));
+  p.lam0 = 1.0;
+  return p;
+}
+
+Problem build_theta(const DTT& a) {
+  const int d = a.d;
+  Problem p;
+  p.d = d;
+  DTT I = tt_identity(d, 2), J = tt_ones_mat(d, 2), E = unit_first(d);
+  DTT part1 = tt_diag(vecv(a));
+  DTT part2 = tt_kron(vecv(E).view(4, 1), vecv(I).view(1, 4));  // vec_TT(E) vec_TT(I)^T
+  p.A_eq = tt_add(part1, part2, 1.0, 1.0);
+  p.B_eq = vecv(E);
+  p.K_y = tt_diag(vecv(tt_add(tt_add(J, a, 1.0, -1.0), E, 1.0, -1.0)));
+  p.C = J;
+  p.lam0 = 2.0;
+  return p;
+}
+
+Problem build_cc(const DTT& cp, const DTT& cm, const DTT& a) {
+  const int d = a.d;
+  Problem p;
+  p.d = d;
+  DTT deg = tt_matvec(cm, ones_vec(d));
+  p.C = tt_add(tt_add(cp, tt_diag(deg), 1.0, 1.0), cm, 1.0, -1.0);
+  DTT I = tt_identity(d, 2), J = tt_ones_mat(d, 2);
+  p.A_eq = tt_diag(vecv(I));
+  p.B_eq = vecv(tt_copy(I));
+  p.K_y = tt_diag(vecv(tt_add(J, I, 1.0, -1.0)));
+  p.ineq = true;
+  p.A_ineq = tt_diag(vecv(a));
+  p.B_ineq = tt_zeros_like_modes(d, 4, 1);
+  p.K_t = tt_diag(vecv(tt_add(J, a, 1.0, -1.0)));
+  p.ones_t = tt_copy(a);
+  p.sgn = 1.0;
+  p.q = (long long)std::llround(tt_inner(vecv(a), vecv(J)));
+  p.lam0 = 2.0;
+  p.lam0_ineq = 1e-3;
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// the interior-point iteration (Algorithm 1 with the choices of Section 3.5)
+// ---------------------------------------------------------------------------
+Solver::Solver(Problem p, const Options& o) : p_(std::move(p)), o_(o) {
+  rnd_.seed = o.seed;
+  rnd_.n = 0;
+  const int d = p_.d;
+  N_ = 1 << d;
+  I_ = tt_identity(d, 2);
+  Z_ = tt_scale(I_, p_.lam0);
+  Y_ = tt_zeros_like_modes(d, 2, 2);
+  if (p_.ineq) {
+    DTT e;
+    double lmin = min_gen_eig(I_, p_.ones_t, &e, false, rnd_, 2, 6, TT_FP64);
+    double alpha_p = lmin < 0 ? p_.lam0 * step_from_lambda(lmin) : p_.lam0;
+    X_ = tt_add(tt_scale(I_, p_.lam0), p_.ones_t, 1.0, alpha_p / 10.0);
+    T_ = tt_scale(p_.ones_t, p_.lam0_ineq);
+  } else {
+    X_ = tt_scale(I_, p_.lam0);
+  }
+  eta_ = o.eta0;
+  nB_ = tt_norm(p_.B_eq);
+  nC_ = tt_norm(vecv(p_.C));
+}
+
+DTT Solver::slack(const DTT& X) {
+  // s = sgn (A_ineq vec X - B_ineq)
+  return tt_add(tt_matvec(p_.A_ineq, vecv(X)), p_.B_ineq, p_.sgn, -p_.sgn);
+}
+
+Solver::Measures Solver::measures() {
+  Measures m;
+  DTT rp = tt_add(p_.B_eq, tt_matvec(p_.A_eq, vecv(X_)), 1.0, -1.0);
+  DTT rd = tt_add(tt_add(vecv(Z_), vecv(p_.C), 1.0, 1.0), tt_matvec(tt_transpose(p_.A_eq), vecv(Y_)), 1.0, -1.0);
+  if (p_.ineq) rd = tt_add(rd, tt_matvec(tt_transpose(p_.A_ineq), vecv(T_)), 1.0, p_.sgn);
+  double comp = tt_inner(vecv(Z_), vecv(X_));
+  if (p_.ineq) comp += tt_inner(vecv(T_), slack(X_));
+  m.pobj = tt_inner(vecv(p_.C), vecv(X_));
+  m.dobj = tt_inner(p_.B_eq, vecv(Y_));
+  if (p_.ineq) m.dobj -= p_.sgn * tt_inner(p_.B_ineq, vecv(T_));
+  m.rel_p = tt_norm(rp) / (1.0 + nB_);
+  m.rel_d = tt_norm(rd) / (1.0 + nC_);
+  m.rel_gap = comp / ((N_ + p_.q) * (1.0 + std::fabs(m.pobj)));
+  m.mu = comp / (N_ + p_.q);
+  return m;
+}
+
+void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, const DTT* ct, const DTT* cs,
+                       bool zero_p, bool zero_d, DTT& dX, DTT& dY, DTT& dT, DTT& dZ, int* sweeps) {
+  const int d = p_.d;
+  NewtonData nd;
+  DTT vI = vecv(I_);
+  DTT idop = tt_identity(d, 4);
+  if (dir == 1) {  // AHO
+    nd.LZ = {op_kron_right(Z_), op_kron_left(Z_)};
+    nd.LX = {op_kron_right(X_), op_kron_left(X_)};
+    nd.rc = {{1.0, op_kron_right(Z_), vecv(X_)}, {1.0, op_kron_left(Z_), vecv(X_)}, {-2.0 * sigma_mu, idop, vI}};
+  } else {  // XZ
+    nd.LZ = {op_kron_left(Z_)};
+    nd.LX = {op_kron_right(X_)};
+    nd.rc = {{1.0, op_kron_left(Z_), vecv(X_)}, {-sigma_mu, idop, vI}};
+  }
+  if (cx) {
+    if (dir == 1) {
+      nd.rc.push_back({1.0, op_kron_right(tt_transpose(*cz)), vecv(*cx)});
+      nd.rc.push_back({1.0, op_kron_left(*cz), vecv(*cx)});
+    } else {
+      nd.rc.push_back({1.0, op_kron_left(*cz), vecv(*cx)});
+    }
+  }
+  if (!zero_p) nd.rp = {{1.0, idop, p_.B_eq}, {-1.0, p_.A_eq, vecv(X_)}};
+  else nd.rp = {{0.0, idop, vI}};
+  if (!zero_d) {
+    nd.rd = {{1.0, idop, vecv(Z_)}, {1.0, idop, vecv(p_.C)}, {-1.0, tt_transpose(p_.A_eq), vecv(Y_)}};
+    if (p_.ineq) nd.rd.push_back({p_.sgn, tt_transpose(p_.A_ineq), vecv(T_)});
+  } else {
+    nd.rd = {{0.0, idop, vI}};
+  }
+  nd.A = p_.A_eq;
+  nd.AT = tt_transpose(p_.A_eq);
+  nd.K = p_.K_y;
+  if (p_.ineq) {
+    nd.ineq = true;
+    DTT vT = vecv(T_), vG = vecv(p_.ones_t);
+    nd.TA = tt_diag(tt_hadamard(vT, vG));
+    DTT s = slack(X_);
+    nd.DK = {tt_diag(s), p_.K_t};
+    nd.AiT = tt_transpose(p_.A_ineq);
+    nd.sgn = p_.sgn;
+    nd.rt = {{1.0, tt_diag(vT), s}, {-sigma_mu, idop, vecv(p_.ones_t)}};
+    if (ct) nd.rt.push_back({1.0, tt_diag(vecv(*ct)), *cs});
+  }
+  AmenInfo info;
+  BlockTT w = amen_solve(nd, d, w_ ? w_.get() : nullptr, eta_, o_.rank_cap, o_.kick, o_.max_sweeps, rnd_,
+                         o_.prec, &info);
+  w_ = std::make_unique<BlockTT>(w);
+  *sweeps = info.sweeps;
+  dX = unvec(w.component(0));
+  dY = unvec(w.component(1));
+  if (p_.ineq) {
+    dT = unvec(w.component(2));
+    dZ = unvec(w.component(3));
+  } else {
+    dZ = unvec(w.component(2));
+  }
+  if (dir == 0) {
+    dX = tt_sym(dX);
+    dY = tt_sym(dY);
+    dZ = tt_sym(dZ);
+    if (p_.ineq) dT = tt_sym(dT);
+  }
+}
+
+double Solver::max_step(const DTT& M, const DTT& dM, DTT* e) {
+  bool warm = (e == &eX_) ? haveX_ : haveZ_;
+  double lam = min_gen_eig(M, tt_sym(dM), e, warm, rnd_, o_.eig_rank, o_.eig_sweeps, TT_FP64);
+  if (e == &eX_) haveX_ = true; else haveZ_ = true;
+  return step_from_lambda(lam);
+}
+
+double Solver::max_step_diag(const DTT& v, const DTT& dv, DTT* e) {
+  DTT idle = tt_add(vecv(tt_ones_mat(p_.d, 2)), vecv(p_.ones_t), 1.0, -1.0);
+  DTT M = tt_diag(tt_add(v, idle, 1.0, 1.0));
+  bool warm = (e == &eS_) ? haveS_ : haveT_;
+  double lam = min_gen_eig(M, tt_diag(dv), e, warm, rnd_, 1, o_.eig_sweeps, TT_FP64);
+  if (e == &eS_) haveS_ = true; else haveT_ = true;
+  return step_from_lambda(lam);
+}
+
+void Solver::steps(const DTT& dX, const DTT& dT, const DTT& dZ, double* ap, double* ad) {
+  double a_p = max_step(X_, dX, &eX_);
+  double a_d = max_step(Z_, dZ, &eZ_);
+  if (p_.ineq) {
+    DTT ds = tt_matvec(p_.A_ineq, vecv(dX));
+    DTT s = slack(X_);
+    double a_s = max_step_diag(s, ds, &eS_);
+    double a_t = max_step_diag(vecv(T_), vecv(dT), &eT_);
+    a_p = std::min(a_p, a_s);
+    a_d = std::min(a_d, a_t);
+  }
+  *ap = std::min(1.0, o_.damping * a_p);
+  *ad = std::min(1.0, o_.damping * a_d);
+}
+
+DTT Solver::round_psd(const DTT& Mx, double delta, const DTT* shift) {
+  double sn = shift ? tt_norm(vecv(*shift)) : 0.0;
+  auto rz = tt_round(vecv(Mx), delta / (1.0 + sn), o_.rank_cap);
+  DTT rounded = unvec(rz.first);
+  double zeta = rz.second;
+  if (shift && zeta > 0) rounded = tt_add(rounded, *shift, 1.0, zeta);
+  if (rounded.maxrank() >= Mx.maxrank() && Mx.maxrank() <= o_.rank_cap) return Mx;
+  return rounded;
+}
+
+IterLog Solver::iterate() {
+  cudaStream_t st = cur_stream();
+  cudaEvent_t e0, e1;
+  TT_CUDA(cudaEventCreate(&e0));
+  TT_CUDA(cudaEventCreate(&e1));
+  TT_CUDA(cudaEventRecord(e0, st));
+  IterLog log;
+  log.iter = it_;
+  Measures ms = measures();
+  log.mu = ms.mu;
+  log.rel_p = ms.rel_p;
+  log.rel_d = ms.rel_d;
+  log.rel_gap = ms.rel_gap;
+  log.pobj = ms.pobj;
+  log.dobj = ms.dobj;
+  const double eps_p = 2.0 * o_.eps_gap, eps_d = 2.0 * o_.eps_gap;
+  const double eps_c = o_.eps_gap / std::sqrt((double)p_.d);
+  TT_CHECK(std::isfinite(ms.mu) && std::isfinite(ms.rel_p) && std::isfinite(ms.rel_d), TT_E_NUMERIC,
+           "non-finite residual");
+  if (ms.rel_p <= eps_p && ms.rel_d <= eps_d && ms.rel_gap <= eps_c) {
+    log.converged = 1;
+  } else {
+    eta_ = std::max(std::min(eta_, o_.eta_C * ms.mu), o_.eta_floor);
+    const int dir = it_ < o_.xz_warmup ? 0 : 1;
+    const bool zp = ms.rel_p <= eps_p, zd = ms.rel_d <= eps_d;
+    DTT dXa, dYa, dTa, dZa;
+    int sw = 0;
+    direction(dir, 0.0, nullptr, nullptr, nullptr, nullptr, zp, zd, dXa, dYa, dTa, dZa, &sw);
+    double apa, ada;
+    steps(dXa, dTa, dZa, &apa, &ada);
+    DTT Xa = tt_add(X_, dXa, 1.0, apa), Za = tt_add(Z_, dZa, 1.0, ada);
+    double mu_aff = tt_inner(vecv(Za), vecv(Xa));
+    DTT dsa;
+    if (p_.ineq) {
+      DTT Ta = tt_add(T_, dTa, 1.0, ada);
+      mu_aff += tt_inner(vecv(Ta), slack(Xa));
+      dsa = tt_matvec(p_.A_ineq, vecv(dXa));
+    }
+    mu_aff /= (N_ + p_.q);
+    double ratio = std::min(1.0, std::max(0.0, mu_aff / ms.mu));
+    double sigma = ratio * ratio * ratio;
+    DTT dX, dY, dT, dZ;
+    direction(dir, sigma * ms.mu, &dXa, &dZa, p_.ineq ? &dTa : nullptr, p_.ineq ? &dsa : nullptr, zp, zd, dX, dY, dT,
+              dZ, &sw);
+    double ap, ad;
+    steps(dX, dT, dZ, &ap, &ad);
+    log.alpha_p = ap;
+    log.alpha_d = ad;
+    log.direction = dir;
+    log.sweeps = sw;
+    log.max_rank_W = w_->frame.maxrank();
+    const double tol_p = eta_ * (1.0 + nB_) / 10.0, tol_d = eta_ * (1.0 + nC_) / 10.0;
+    X_ = round_psd(tt_add(X_, dX, 1.0, ap), tol_p, &I_);
+    Z_ = round_psd(tt_add(Z_, dZ, 1.0, ad), tol_d, &I_);
+    Y_ = round_psd(tt_add(Y_, dY, 1.0, ad), tol_d, nullptr);
+    if (p_.ineq) T_ = round_psd(tt_add(T_, dT, 1.0, ad), tol_d, &p_.ones_t);
+    ++it_;
+  }
+  log.max_rank_X = X_.maxrank();
+  log.max_rank_Z = Z_.maxrank();
+  TT_CUDA(cudaEventRecord(e1, st));
+  TT_CUDA(cudaEventSynchronize(e1));
+  float msec = 0.f;
+  TT_CUDA(cudaEventElapsedTime(&msec, e0, e1));
+  log.seconds = msec * 1e-3;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return log;
+}
+
+}  // namespace ttsdp

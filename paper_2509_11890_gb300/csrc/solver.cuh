@@ -1,0 +1,93 @@
+// The TT interior-point solver: problem assembly (Section 4), block-AMEn
+// Newton solves (Section 3.3), step lengths (Section 3.4) and Algorithm 1.
+#pragma once
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "tt.cuh"
+
+namespace ttsdp {
+
+struct Problem {
+  int d = 0;
+  DTT C, A_eq, B_eq, K_y;                 // C: 2x2 modes; operators 4x4; B_eq mode 4
+  bool ineq = false;
+  DTT A_ineq, B_ineq, K_t, ones_t;
+  double sgn = 1.0;
+  long long q = 0;
+  double lam0 = 1.0, lam0_ineq = 1e-3;
+};
+
+Problem build_maxcut(const DTT& weights);
+Problem build_theta(const DTT& adjacency);
+Problem build_cc(const DTT& c_plus, const DTT& c_minus, const DTT& adjacency);
+
+// Block TT (Definition "Block Tensor-Train") with the block index at core 0.
+struct BlockTT {
+  DTT frame;                              // vector TT (mode 4); core 0 = block 0
+  int nblk = 0;
+  std::shared_ptr<DBuf<double>> block;    // nblk x r0 x 4 x r1
+  DTT component(int b) const;
+};
+
+struct Options {
+  double eps_gap = 1e-4;
+  int rank_cap = 16;
+  int xz_warmup = 3;
+  double eta0 = 1e-3, eta_floor = 1e-4, eta_C = 2.0, damping = 0.95;
+  int prec = 0;
+  int max_iters = 60, max_sweeps = 4, kick = 4, eig_rank = 4, eig_sweeps = 4;
+  uint64_t seed = 1234;
+};
+
+struct IterLog {
+  int iter = 0, converged = 0, direction = 0, sweeps = 0;
+  double mu = 0, rel_p = 0, rel_d = 0, rel_gap = 0, pobj = 0, dobj = 0, alpha_p = 0, alpha_d = 0;
+  int max_rank_X = 0, max_rank_Z = 0, max_rank_W = 0;
+  double seconds = 0;
+};
+
+class Solver {
+ public:
+  Solver(Problem p, const Options& o);
+  IterLog iterate();        // one iteration of Algorithm 1
+  const DTT& X() const { return X_; }
+  const DTT& Y() const { return Y_; }
+  const DTT& T() const { return T_; }
+  const DTT& Z() const { return Z_; }
+  bool has_ineq() const { return p_.ineq; }
+  int order() const { return p_.d; }
+  int iter() const { return it_; }
+  const Options& options() const { return o_; }
+
+ private:
+  struct Measures {
+    double rel_p, rel_d, rel_gap, pobj, dobj, mu;
+  };
+  Measures measures();
+  DTT slack(const DTT& X);
+  void direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, const DTT* ct, const DTT* cs,
+                 bool zero_p, bool zero_d, DTT& dX, DTT& dY, DTT& dT, DTT& dZ, int* sweeps);
+  void steps(const DTT& dX, const DTT& dT, const DTT& dZ, double* ap, double* ad);
+  double max_step(const DTT& M, const DTT& dM, DTT* e);
+  double max_step_diag(const DTT& v, const DTT& dv, DTT* e);
+  DTT round_psd(const DTT& M, double delta, const DTT* shift);
+
+  Problem p_;
+  Options o_;
+  Counter rnd_;
+  DTT I_, X_, Y_, T_, Z_;
+  double eta_, nB_, nC_;
+  int it_ = 0, N_;
+  std::unique_ptr<BlockTT> w_;
+  DTT eX_, eZ_, eT_, eS_;
+  bool haveX_ = false, haveZ_ = false, haveT_ = false, haveS_ = false;
+};
+
+// Exposed for tests through the C ABI: min over e of <e, dM e>/<e, M e>.
+double min_gen_eig(const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank, int sweeps,
+                   int prec);
+
+}  // namespace ttsdp

@@ -1,0 +1,24 @@
+// Tensor-core (tcgen05 / TMEM, TMA-fed) path for the heavy middle stage of
+// the environment update and the local product:
+//   T2[a'][i][q][b] = sum_{p,j} Op[p][i][j][q] T1[a'][p][j][b]
+// for TF32 or BF16 inputs with FP32 accumulation.
+#pragma once
+
+#include "common.cuh"
+
+namespace ttsdp {
+
+// Returns true when the stage was executed on the tensor cores (TF32 / BF16
+// precisions with float operands); false lets the caller run the SIMT path.
+template <typename T>
+bool tc_stage2(int prec, long long rw, long long R, long long R2, long long m, long long n,
+               long long rv2, const T* op, const T* t1, T* t2, cudaStream_t st);
+
+// Plain tensor-core GEMM C[b] (M x N, fp32 row-major) = A[b] (M x K) * B[b] (N x K)^T,
+// both operands K-major in the given element type (TT_MIXED_TF32: fp32 storage
+// read as TF32; TT_MIXED_BF16: bf16 storage). Used by stage 2 and by the
+// benchmark's kernel timing.
+void tc_gemm_tn(int prec, int M, int N, int K, int batch, const void* A, long long sA,
+                const void* B, long long sB, float* C, long long sC, cudaStream_t st);
+
+}  // namespace ttsdp

@@ -1,0 +1,153 @@
+"""GPU parity of the contraction, TT-arithmetic and rounding kernels against the oracle.
+
+Every call goes through the C ABI (via the ctypes binding); expected values
+come from the oracle only. FP64 results must match to 1e-11 relative; FP32
+contractions to 2e-5 relative (single-precision accumulation over at most a
+few thousand terms).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2509_11890_gb300 as tg  # noqa: E402
+from oracle import tt  # noqa: E402
+from paper_2509_11890_gb300 import inputs  # noqa: E402
+
+DEV = "cuda"
+
+# (rw, rw2, R, R2, rv, rv2, m, n): small, tile-spanning with ragged tails, boundary, 2x2 modes, bench-sized
+SHAPES = [
+    (1, 4, 1, 2, 1, 3, 4, 4),
+    (3, 70, 5, 33, 2, 65, 4, 4),
+    (17, 9, 7, 3, 66, 5, 4, 4),
+    (5, 6, 3, 4, 7, 2, 2, 2),
+    (16, 16, 32, 32, 16, 16, 4, 4),
+    (64, 64, 128, 128, 64, 64, 4, 4),
+]
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _rand(shape, seed):
+    return inputs.rng(seed, 77).standard_normal(shape)
+
+
+def _dims(s):
+    return dict(zip(["rw", "rw2", "R", "R2", "rv", "rv2", "m", "n"], s))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec,tol", [(tg.FP64, 1e-11), (tg.FP32, 2e-5)])
+def test_env_left_step(shape, prec, tol):
+    rw, rw2, R, R2, rv, rv2, m, n = shape
+    phi, u = _rand((rw, R, rv), 1), _rand((rw, m, rw2), 2)
+    op, v = _rand((R, m, n, R2), 3), _rand((rv, n, rv2), 4)
+    ref = tt.env_left_step(phi, u, op, v)
+    out = torch.empty(rw2 * R2 * rv2, dtype=torch.float64, device=DEV)
+    tg.env_left_step(_dims(shape), _t(phi), _t(u), _t(op), _t(v), out, prec)
+    assert _rel(out.cpu().numpy().reshape(ref.shape), ref) <= tol
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec,tol", [(tg.FP64, 1e-11), (tg.FP32, 2e-5)])
+def test_env_right_step(shape, prec, tol):
+    rw, rw2, R, R2, rv, rv2, m, n = shape
+    psi, u = _rand((rw2, R2, rv2), 5), _rand((rw, m, rw2), 6)
+    op, v = _rand((R, m, n, R2), 7), _rand((rv, n, rv2), 8)
+    ref = tt.env_right_step(psi, u, op, v)
+    out = torch.empty(rw * R * rv, dtype=torch.float64, device=DEV)
+    tg.env_right_step(_dims(shape), _t(psi), _t(u), _t(op), _t(v), out, prec)
+    assert _rel(out.cpu().numpy().reshape(ref.shape), ref) <= tol
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec,tol", [(tg.FP64, 1e-11), (tg.FP32, 2e-5)])
+def test_local_apply(shape, prec, tol):
+    rw, rw2, R, R2, rv, rv2, m, n = shape
+    phi, psi = _rand((rw, R, rv), 9), _rand((rw2, R2, rv2), 10)
+    op, x = _rand((R, m, n, R2), 11), _rand((rv, n, rv2), 12)
+    ref = tt.local_apply(phi, op, psi, x)
+    y = torch.empty(rw * m * rw2, dtype=torch.float64, device=DEV)
+    tg.local_apply(_dims(shape), _t(phi), _t(op), _t(psi), _t(x), y, prec)
+    assert _rel(y.cpu().numpy().reshape(ref.shape), ref) <= tol
+
+
+@pytest.mark.parametrize("shape", SHAPES[:5])
+def test_local_matrix(shape):
+    rw, rw2, R, R2, rv, rv2, m, n = shape
+    phi, psi = _rand((rw, R, rv), 13), _rand((rw2, R2, rv2), 14)
+    op = _rand((R, m, n, R2), 15)
+    ref = tt.local_matrix(phi, op, psi)
+    out = torch.empty(ref.size, dtype=torch.float64, device=DEV)
+    tg.local_matrix(_dims(shape), _t(phi), _t(op), _t(psi), out, tg.FP64)
+    assert _rel(out.cpu().numpy().reshape(ref.shape), ref) <= 1e-11
+
+
+def _rtt(dims, rk, seed, mat=False):
+    d = len(dims)
+    ranks = [1] + [rk] * (d - 1) + [1]
+    if mat:
+        return inputs.random_tt_matrix(dims, dims, ranks, seed)
+    return inputs.random_tt(dims, ranks, seed)
+
+
+def test_hadamard_matvec_inner():
+    a = _rtt([2] * 5, 3, 21, mat=True)
+    b = _rtt([2] * 5, 4, 22, mat=True)
+    got = tg.hadamard(tg.DevTT.from_cores(a), tg.DevTT.from_cores(b)).cores()
+    ref = tt.hadamard(a, b)
+    for g, r in zip(got, ref):
+        np.testing.assert_allclose(g, r, rtol=0, atol=1e-13 * np.abs(r).max())
+    op = inputs.random_tt_matrix([4] * 4, [4] * 4, [1, 2, 3, 2, 1], 23)
+    v = _rtt([4] * 4, 3, 24)
+    got = tg.matvec(tg.DevTT.from_cores(op), tg.DevTT.from_cores(v)).cores()
+    np.testing.assert_allclose(tt.full_vec(got), tt.full_vec(tt.matvec(op, v)), rtol=1e-12,
+                               atol=1e-12 * np.abs(tt.full_vec(tt.matvec(op, v))).max())
+    u, w = _rtt([4] * 6, 5, 25), _rtt([4] * 6, 3, 26)
+    val = tg.inner(tg.DevTT.from_cores(u), tg.DevTT.from_cores(w))
+    assert math.isclose(val, tt.inner(u, w), rel_tol=1e-11, abs_tol=1e-11)
+
+
+@pytest.mark.parametrize("d,rk,seed", [(5, 6, 30), (8, 12, 31), (10, 20, 32)])
+def test_round_ranks_and_error(d, rk, seed):
+    base = _rtt([4] * d, max(2, rk // 3), seed)
+    noise = tt.scale(_rtt([4] * d, rk, seed + 100), 1e-6)
+    s = tt.add(base, noise)
+    nrm = tt.norm(s)
+    delta = 1e-4 * nrm
+    ref, zeta_ref, ties = tt.round_tt(s, delta)
+    got, zeta = tg.round_tt(tg.DevTT.from_cores(s), delta)
+    # ranks bit-exact on bonds that are not ties
+    for k, (rg, rr) in enumerate(zip(got.ranks, tt.ranks(ref))):
+        if 0 < k < d and not ties[k - 1]:
+            assert rg == rr, (k, got.ranks, tt.ranks(ref))
+    assert math.isclose(zeta, zeta_ref, rel_tol=1e-8, abs_tol=1e-13 * nrm)
+    if d <= 8:
+        np.testing.assert_allclose(tt.full_vec(got.cores()), tt.full_vec(ref), atol=1e-10 * nrm)
+    else:
+        # the rounded tensor differs from the input by exactly zeta
+        diff = tt.add(got.cores(), s, 1.0, -1.0)
+        assert math.isclose(tt.norm(diff), zeta, rel_tol=1e-6, abs_tol=1e-12 * nrm)
+
+
+def test_round_cap_and_degenerate():
+    s = tt.add(_rtt([4] * 6, 5, 40), _rtt([4] * 6, 4, 41))
+    ref, zr, _ = tt.round_tt(s, 0.0, cap=3)
+    got, zg = tg.round_tt(tg.DevTT.from_cores(s), 0.0, cap=3)
+    assert got.ranks == tt.ranks(ref)
+    assert math.isclose(zg, zr, rel_tol=1e-9)
+    # d = 1 and rank-1 inputs round to themselves
+    one = [inputs.rng(42).standard_normal((1, 4, 1))]
+    g1, z1 = tg.round_tt(tg.DevTT.from_cores(one), 1e-3)
+    np.testing.assert_allclose(g1.cores()[0], one[0], atol=1e-15)
+    assert z1 == 0.0

@@ -1,0 +1,70 @@
+"""GPU parity of the full TT interior-point solver against the dense SDP optimum
+(oracle O2) and the oracle TT-IPM (O4) on the same seeded instances."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2509_11890_gb300 as tg  # noqa: E402
+from oracle import sdp_dense as sd, tt, tt_ipm, tt_problems as tp  # noqa: E402
+from paper_2509_11890_gb300 import inputs  # noqa: E402
+
+
+def _opts(**kw):
+    base = dict(rank_cap=16, max_iters=40)
+    base.update(kw)
+    return tg.default_options(**base)
+
+
+@pytest.mark.parametrize("d,seed", [(3, 0), (4, 2), (5, 1)])
+def test_maxcut_reaches_dense_optimum(d, seed):
+    inst = inputs.maxcut_kron(d, seed)
+    ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]))
+    ctx = tg.Context.maxcut(inst["adjacency_cores"], _opts())
+    res = ctx.solve()
+    assert res["status"] == 0, res
+    assert abs(res["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3
+    assert res["rel_gap"] <= 1e-4 / math.sqrt(d)
+    X = tt.full_mat(ctx.iterate(0))
+    assert np.linalg.eigvalsh(0.5 * (X + X.T))[0] > 0
+    np.testing.assert_allclose(np.diag(X), 1.0, atol=5e-3)
+
+
+def test_maxcut_trajectory_matches_oracle_ipm():
+    # same algorithm, same counter stream: the first iterations agree closely
+    d = 4
+    inst = inputs.maxcut_kron(d, 3)
+    prob = tp.maxcut(inst["adjacency_cores"], d)
+    o4 = tt_ipm.TTIPM(prob, tt_ipm.Options(rank_cap=16, max_iters=40))
+    ctx = tg.Context.maxcut(inst["adjacency_cores"], _opts())
+    for it in range(3):
+        info = ctx.newton_step()
+        o4.iterate(it)
+        h = o4.history[-1]
+        assert math.isclose(info["pobj"], h.pobj, rel_tol=1e-6, abs_tol=1e-8), (it, info["pobj"], h.pobj)
+        assert math.isclose(info["mu"], h.mu, rel_tol=1e-6), (it, info["mu"], h.mu)
+
+
+def test_theta_reaches_dense_optimum():
+    d = 3
+    inst = inputs.theta_hypercube_kron(d, 0)
+    ref = sd.solve_dense(sd.theta_sdp(inst["adjacency"]))
+    a = tp.graph_tt(inst["adjacency"])
+    ctx = tg.Context.theta(a, _opts(max_iters=60))
+    res = ctx.solve()
+    assert res["status"] == 0, res
+    assert abs(res["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 5e-3
+
+
+def test_cc_reaches_dense_optimum():
+    d = 3
+    inst = inputs.cc_signed(d, 1)
+    ref = sd.solve_dense(sd.cc_sdp(inst["c_plus"], inst["c_minus"], inst["adjacency"]))
+    ctx = tg.Context.cc(tp.graph_tt(inst["c_plus"]), tp.graph_tt(inst["c_minus"]), tp.graph_tt(inst["adjacency"]),
+                        _opts(max_iters=60))
+    res = ctx.solve()
+    assert res["status"] == 0, res
+    assert abs(res["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 5e-3
