@@ -1,0 +1,293 @@
+"""Benchmark: time-to-gap of the GB300 TT interior-point method on the
+configured Max-Cut workload, with contraction throughput, roofline, an
+end-to-end number through the C ABI from host buffers, and the oracle timed
+on the host cores.
+
+Default workload: Max-Cut SDP, n = 2^10 vertices (d = 10 TT cores, 2 x 2
+modes): seeded Kronecker graph (six... ten seeded 2x2 0/1 patterns) OR-ed with
+a seeded Erdos-Renyi graph of edge probability 2/n, edge weights U[0.5, 1.5];
+TT rank cap 64; target gap 1e-4.
+
+One step is one interior-point iteration (Algorithm 1: residuals, mu, the
+Mehrotra predictor and corrector block-AMEn Newton solves, step lengths,
+update and rounding). The timed region runs K steps of one solve from its
+initial point; the solve's time-to-gap is the time of the steps up to the
+first iteration at which the stopping rules hold.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "maxcut_d10_kron_er_cap64": dict(kind="maxcut_er", d=10, cap=64),
+    "maxcut_d6_kron_cap16": dict(kind="maxcut", d=6, cap=16),
+}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=12)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="maxcut_d10_kron_er_cap64", choices=sorted(WORKLOADS))
+    p.add_argument("--precision", default="fp32", choices=sorted(PREC))
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _instance(w, seed):
+    from paper_2509_11890_gb300 import inputs
+    if w["kind"] == "maxcut_er":
+        return inputs.maxcut_kron_er(w["d"], seed)
+    return inputs.maxcut_kron(w["d"], seed)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.stop = threading.Event()
+        self.t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self.stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for ln in out.stdout.strip().splitlines():
+                    self.rows.append([x.strip() for x in ln.split(",")])
+            except Exception:
+                pass
+            self.stop.wait(0.2)
+
+    def __enter__(self):
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(a):
+    """The oracle on the host cores: dense primal-dual IPM (O2) to the target gap on the same instance."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import sdp_dense as sd
+    w = WORKLOADS[a.workload]
+    inst = _instance(w, a.seed)
+    p = sd.maxcut_sdp(inst["weights"])
+    times = []
+    res = None
+    for _ in range(max(a.steps, 1)):
+        t0 = time.perf_counter()
+        res = sd.solve_dense(p, tol=1e-4)
+        times.append(time.perf_counter() - t0)
+    val = float(np.median(times))
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "time-to-gap-1e-4 (s)", "value": val, "unit": "s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": val * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "n": 2 ** w["d"], "d": w["d"], "seed": a.seed},
+        "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": "dense HKM primal-dual IPM (oracle O2) on the same instance to relative gap 1e-4, "
+                                   f"{res.iters} iterations, median of {len(times)} solves"},
+        "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_pobj": res.pobj,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _cpu_baseline(w, seed, budget_s=30.0):
+    """Oracle O2 time-to-gap on the same instance (bounded: one solve, ~10-30 s of CPU work)."""
+    from oracle import sdp_dense as sd
+    inst = _instance(w, seed)
+    p = sd.maxcut_sdp(inst["weights"])
+    t0 = time.perf_counter()
+    res = sd.solve_dense(p, tol=1e-4, max_iter=60)
+    dt = time.perf_counter() - t0
+    return {"value": dt, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one dense HKM IPM solve (oracle O2) of the same n={2 ** w['d']} instance to relative gap "
+                      f"1e-4 ({res.iters} iterations, pobj {res.pobj:.6f})"}, res.pobj
+
+
+def run_ours(a):
+    import torch
+
+    import paper_2509_11890_gb300 as tg
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WORKLOADS[a.workload]
+    seed = a.seed + rank  # replicas: one independent instance per rank
+    inst = _instance(w, seed)
+    stream = torch.cuda.current_stream()
+    # row a1 (setup, untimed): graph -> TT on the device
+    if inst.get("adjacency_cores") is not None:
+        wcores = inst["adjacency_cores"]
+    else:
+        wcores = tg.tt_from_dense(torch.from_numpy(inst["weights"]).cuda(), eps_rel=1e-13)
+    w_ranks = [c.shape[0] for c in wcores] + [1]
+    opts = tg.default_options(rank_cap=w["cap"], precision=PREC[a.precision], max_iters=a.steps + 2)
+    # warm-up: W iterations of a throwaway solve
+    ctx = tg.Context.maxcut(wcores, opts)
+    for _ in range(a.warmup):
+        ctx.newton_step()
+    ctx.close()
+    torch.cuda.synchronize()
+    # timed region: K iterations of one solve from its initial point
+    ctx = tg.Context.maxcut(wcores, opts)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    tg.contraction_stats_reset()
+    l0 = tg.launch_count()
+    infos = []
+    with Clocks(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(a.steps):
+            infos.append(ctx.newton_step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total = ev0.elapsed_time(ev1) * 1e-3
+    launches = tg.launch_count() - l0
+    cflops, csec = tg.contraction_stats()
+    conv = [i for i in infos if i["converged"]]
+    reached = bool(conv)
+    ttg = sum(i["seconds"] for i in infos if not i["converged"]) if reached else total
+    last = conv[0] if reached else infos[-1]
+    if world > 1:
+        t = torch.tensor([ttg, total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ttg, total = float(t[0]), float(t[1])
+    # end to end through the C ABI with host buffers: H2D of the weight cores,
+    # the solve, D2H of the primal iterate X
+    e2e = None
+    if not a.no_e2e:
+        h2d = int(sum(c.size for c in wcores) * 8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2 = tg.Context.maxcut(wcores, opts)
+        n_e2e = 0
+        for _ in range(a.steps):
+            info = ctx2.newton_step()
+            n_e2e += 1
+            if info["converged"]:
+                break
+        X = ctx2.iterate(0)
+        torch.cuda.synchronize()
+        e2e_t = time.perf_counter() - t0
+        ctx2.close()
+        e2e = {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(sum(c.size for c in X) * 8),
+               "steps": n_e2e, "gap_reached": bool(info["converged"])}
+    peaks, peak_kind = _peaks()
+    if a.precision == "fp64":
+        bound, peak, punit = "alu", 1.25, "TFLOP/s"  # FP64 FMA rate of GB300 (nominal; 1.2547 measured)
+        peak_note = "FP64 ALU peak, nominal 1.25 TFLOP/s (probe measured 1.25)"
+    elif a.precision == "fp32":
+        bound, peak, punit = "alu", 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
+        peak_note = "FP32 ALU peak from 152 SMs x 128 lanes x 2 flops x max SM clock"
+    else:
+        ratio = 0.5 if a.precision == "tf32" else 1.0
+        bound, peak, punit = "tensor", peaks["bf16_tflops_sustained"] * ratio, "TFLOP/s"
+        peak_note = f"{peak_kind} bf16 sustained x {ratio} (nominal dtype ratio)"
+    achieved = cflops / csec / 1e12 if csec > 0 else 0.0
+    line = {
+        "metric": "time-to-gap-1e-4 (s)", "value": ttg, "unit": "s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total / a.steps * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[a.precision], "data": "synthetic",
+        "config": {"workload": a.workload, "n": 2 ** w["d"], "d": w["d"], "rank_cap": w["cap"], "seed": a.seed,
+                   "weights_tt_max_rank": max(w_ranks), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set per step far exceeds L2 traffic reuse; no flush"},
+        "gap_reached": reached,
+        "final": {k: last[k] for k in ("iter", "rel_gap", "rel_p", "rel_d", "pobj", "dobj", "mu", "max_rank_X",
+                                       "max_rank_Z", "max_rank_W", "gmres_iters")},
+        "contraction_tflops": achieved,
+        "contraction_share": csec / total if total > 0 else None,
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
+                     "frac": achieved / peak if peak else None, "traffic": None, "peak_source": peak_note,
+                     "kernel": "environment / local-product contraction (three strided GEMM stages)"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if rank == 0:
+        cpu, opt = _cpu_baseline(w, a.seed)
+        line["cpu_baseline"] = cpu
+        line["oracle_pobj"] = opt
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -141,6 +141,16 @@ tt_status tt_round(const tt_desc* in, double delta, int32_t rank_cap, int32_t* r
                    double* cores_out, size_t capacity, double* zeta_out, int32_t precision,
                    void* stream);
 
+/* Row a1 helper: TT decomposition (TT-SVD of Oseledets, as Section 4 notes
+ * one may do for operators given as matrices) of a dense n^d x n^d matrix,
+ * row-major FP64 on the DEVICE, in its vec_TT order: a TT matrix with n x n
+ * modes. Bond k keeps the smallest rank whose discarded energy is at most
+ * (eps_rel ||M||_F)^2 / (d-1), then at most rank_cap (<= 0: none).
+ * ranks_out (host, d+1), cores_out (host, capacity doubles; NULL = size query:
+ * *count receives the number of doubles). FP64 throughout. */
+tt_status tt_from_dense(const double* dense, int32_t d, int32_t n, double eps_rel, int32_t rank_cap,
+                        int32_t* ranks_out, double* cores_out, size_t* count, void* stream);
+
 /* ---------------------------------------------------------------------------
  * The solver (rows a1-a5, a10-a12): a context holds one SDP in TT form and
  * its iterates on the device.
@@ -181,6 +191,10 @@ typedef struct {
   int32_t eig_rank;    /* TT rank of the step-length eigenvector                       */
   int32_t eig_sweeps;
   uint64_t seed;       /* SplitMix64 counter stream seed                               */
+  int32_t local_dense_max; /* reduced local systems up to this size are solved by LU,
+                              larger ones matrix-free by restarted GMRES             */
+  int32_t gmres_restart;
+  int32_t gmres_max_iters; /* operator products per local solve                       */
 } tt_sdp_options;
 
 typedef struct tt_sdp_ctx tt_sdp_ctx;
@@ -192,6 +206,7 @@ typedef struct {
   int32_t max_rank_X, max_rank_Z, max_rank_W, sweeps;
   int32_t direction;   /* 0 XZ, 1 AHO                                                 */
   double seconds;      /* device time of the iteration (CUDA events)                 */
+  int64_t gmres_iters; /* local GMRES operator products so far                       */
 } tt_sdp_iter_info;
 
 typedef struct {
@@ -252,6 +267,11 @@ uint64_t tt_launch_count(void);
  * their algorithmic flop count (for the contraction TFLOP/s metric). */
 void tt_contraction_stats(double* flops, double* seconds);
 void tt_contraction_stats_reset(void);
+/* Per-phase host wall time accumulated while the environment variable
+ * TTSDP_PROFILE=1 is set (each phase then synchronises the stream): one
+ * "name seconds" line per phase, written NUL-terminated into buf (at most cap
+ * bytes); returns the full text length. */
+size_t tt_profile_report(char* buf, size_t cap);
 
 #ifdef __cplusplus
 }

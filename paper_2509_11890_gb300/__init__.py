@@ -19,7 +19,7 @@ FP64, FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
 __all__ = [
     "FP64", "FP32", "MIXED_TF32", "MIXED_BF16", "TTSDPError", "lib",
     "env_left_step", "env_right_step", "local_apply", "local_matrix",
-    "hadamard", "matvec", "inner", "round_tt", "default_options", "Context",
+    "hadamard", "matvec", "inner", "round_tt", "tt_from_dense", "default_options", "Context",
     "launch_count", "contraction_stats", "contraction_stats_reset",
 ]
 
@@ -171,6 +171,30 @@ def round_tt(a: DevTT, delta: float, cap: int = 0, stream=None):
     return DevTT(rr, a.m, a.n, out[:_count(rr, a.m * a.n, 1)].clone()), zeta.value
 
 
+def tt_from_dense(dense, eps_rel=1e-13, cap=0, stream=None):
+    """TT-matrix cores (host numpy, r x n x n x r') of a dense n^d x n^d device matrix (row a1)."""
+    import torch
+    assert dense.is_cuda and dense.dtype == torch.float64
+    N = dense.shape[0]
+    d = int(round(np.log2(N)))
+    assert 2 ** d == N and dense.shape == (N, N)
+    ranks = (ctypes.c_int32 * (d + 1))()
+    cnt = ctypes.c_size_t(0)
+    dense = dense.contiguous()
+    _check(lib().tt_from_dense(_ptr(dense), d, 2, float(eps_rel), int(cap), ranks, None, ctypes.byref(cnt),
+                               _stream(stream)), "tt_from_dense")
+    buf = np.empty(cnt.value, dtype=np.float64)
+    _check(lib().tt_from_dense(_ptr(dense), d, 2, float(eps_rel), int(cap), ranks, buf.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(cnt), _stream(stream)), "tt_from_dense")
+    r = list(ranks)
+    out, off = [], 0
+    for k in range(d):
+        size = r[k] * 4 * r[k + 1]
+        out.append(buf[off:off + size].reshape(r[k], 2, 2, r[k + 1]).copy())
+        off += size
+    return out
+
+
 # --- the solver (rows a1-a5, a10-a12) ----------------------------------------
 
 def default_options(**kw) -> _lib.Options:
@@ -280,3 +304,14 @@ def contraction_stats():
 
 def contraction_stats_reset():
     lib().tt_contraction_stats_reset()
+
+
+def profile_report() -> dict:
+    """Per-phase seconds collected when TTSDP_PROFILE=1 is set."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    lib().tt_profile_report(buf, len(buf))
+    out = {}
+    for ln in buf.value.decode().splitlines():
+        k, v = ln.split()
+        out[k] = float(v)
+    return out

@@ -34,14 +34,16 @@ class Options(ctypes.Structure):
     _fields_ = [("eps_gap", c_double), ("rank_cap", c_int32), ("xz_warmup", c_int32),
                 ("eta0", c_double), ("eta_floor", c_double), ("eta_C", c_double), ("damping", c_double),
                 ("precision", c_int32), ("max_iters", c_int32), ("max_sweeps", c_int32), ("kick", c_int32),
-                ("eig_rank", c_int32), ("eig_sweeps", c_int32), ("seed", ctypes.c_uint64)]
+                ("eig_rank", c_int32), ("eig_sweeps", c_int32), ("seed", ctypes.c_uint64),
+                ("local_dense_max", c_int32), ("gmres_restart", c_int32), ("gmres_max_iters", c_int32)]
 
 
 class IterInfo(ctypes.Structure):
     _fields_ = [("iter", c_int32), ("converged", c_int32), ("mu", c_double), ("rel_p", c_double),
                 ("rel_d", c_double), ("rel_gap", c_double), ("pobj", c_double), ("dobj", c_double),
                 ("alpha_p", c_double), ("alpha_d", c_double), ("max_rank_X", c_int32), ("max_rank_Z", c_int32),
-                ("max_rank_W", c_int32), ("sweeps", c_int32), ("direction", c_int32), ("seconds", c_double)]
+                ("max_rank_W", c_int32), ("sweeps", c_int32), ("direction", c_int32), ("seconds", c_double),
+                ("gmres_iters", ctypes.c_int64)]
 
 
 class Result(ctypes.Structure):
@@ -65,6 +67,8 @@ SIGNATURES = {
     "tt_inner": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), P_double, c_void_p]),
     "tt_round": (c_int32, [ctypes.POINTER(TTDesc), c_double, c_int32, P_int32, c_void_p, c_size_t, P_double,
                            c_int32, c_void_p]),
+    "tt_from_dense": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_int32, P_int32, c_void_p,
+                                ctypes.POINTER(c_size_t), c_void_p]),
     "tt_sdp_default_options": (None, [ctypes.POINTER(Options)]),
     "tt_sdp_create": (c_int32, [ctypes.POINTER(Problem), ctypes.POINTER(Options), c_void_p, ctypes.POINTER(c_void_p)]),
     "tt_sdp_create_maxcut": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(Options), c_void_p,
@@ -83,6 +87,7 @@ SIGNATURES = {
     "tt_launch_count": (ctypes.c_uint64, []),
     "tt_contraction_stats": (None, [P_double, P_double]),
     "tt_contraction_stats_reset": (None, []),
+    "tt_profile_report": (c_size_t, [ctypes.c_char_p, c_size_t]),
 }
 
 _LIB = None

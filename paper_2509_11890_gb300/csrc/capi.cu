@@ -19,6 +19,22 @@ struct StreamGuard {
   ~StreamGuard() { StreamScope::current() = prev; }
 };
 
+// The solver allocates many small scratch buffers stream-ordered; keep freed
+// blocks in the device's default pool instead of returning them to the driver
+// at every synchronisation (the pool's default release threshold is 0).
+void keep_pool_memory() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  static thread_local int done_for = -1;
+  if (done_for == dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done_for = dev;
+}
+
 template <typename F>
 tt_status guarded(void* stream, F&& fn) {
   try {
@@ -29,6 +45,7 @@ tt_status guarded(void* stream, F&& fn) {
       g_last_error = "no CUDA device";
       return TT_E_CUDA;
     }
+    keep_pool_memory();
     fn();
     g_last_error.clear();
     return TT_OK;
@@ -82,6 +99,11 @@ Options to_options(const tt_sdp_options* o) {
   r.eig_rank = o->eig_rank;
   r.eig_sweeps = o->eig_sweeps;
   r.seed = o->seed;
+  r.local_dense_max = o->local_dense_max;
+  r.gmres_restart = o->gmres_restart;
+  r.gmres_max_iters = o->gmres_max_iters;
+  TT_CHECK(r.local_dense_max >= 0 && r.gmres_restart > 0 && r.gmres_max_iters > 0, TT_E_INVALID_ARG,
+           "invalid local solver options");
   TT_CHECK(r.rank_cap > 0 && r.max_sweeps > 0 && r.eig_sweeps > 0 && r.eig_rank > 0 && r.kick >= 0,
            TT_E_INVALID_ARG, "invalid options");
   TT_CHECK(r.prec >= TT_FP64 && r.prec <= TT_MIXED_BF16, TT_E_INVALID_ARG, "unknown precision");
@@ -215,6 +237,22 @@ tt_status tt_round(const tt_desc* in, double delta, int32_t rank_cap, int32_t* r
   });
 }
 
+tt_status tt_from_dense(const double* dense, int32_t d, int32_t n, double eps_rel, int32_t rank_cap,
+                        int32_t* ranks_out, double* cores_out, size_t* count, void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(dense && ranks_out && count && d >= 1 && n >= 1 && eps_rel >= 0.0, TT_E_INVALID_ARG,
+             "bad tt_from_dense arguments");
+    DTT t = tt_from_dense(dense, d, n, eps_rel, rank_cap);
+    for (int k = 0; k <= d; ++k) ranks_out[k] = t.r[k];
+    size_t need = t.count();
+    if (cores_out) {
+      TT_CHECK(*count >= need, TT_E_NOMEM, "capacity too small");
+      tt_to_host(t, cores_out);
+    }
+    *count = need;
+  });
+}
+
 void tt_sdp_default_options(tt_sdp_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
@@ -232,6 +270,9 @@ void tt_sdp_default_options(tt_sdp_options* o) {
   o->eig_rank = 4;
   o->eig_sweeps = 4;
   o->seed = 1234;
+  o->local_dense_max = 4096;
+  o->gmres_restart = 40;
+  o->gmres_max_iters = 400;
 }
 
 static tt_status make_ctx(Problem p, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
@@ -331,6 +372,7 @@ tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info) {
     info->sweeps = l.sweeps;
     info->direction = l.direction;
     info->seconds = l.seconds;
+    info->gmres_iters = l.gmres_iters;
   });
 }
 
@@ -394,3 +436,14 @@ void tt_sdp_destroy(tt_sdp_ctx* ctx) {
 }
 
 }  // extern "C"
+
+extern "C" size_t tt_profile_report(char* buf, size_t cap) {
+  std::string s;
+  for (auto& p : Profiler::table()) s += p.first + " " + std::to_string(p.second) + "\n";
+  if (buf && cap) {
+    size_t n = s.size() < cap - 1 ? s.size() : cap - 1;
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return s.size();
+}

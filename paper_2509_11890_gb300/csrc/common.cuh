@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstdlib>
+#include <ctime>
 #include <cstdio>
 #include <stdexcept>
 #include <string>
@@ -88,5 +90,53 @@ struct LaunchCounter {
 inline void count_launch() { ++LaunchCounter::value(); }
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// Phase timer for diagnosing where an iteration spends its time. Enabled by
+// the environment variable TTSDP_PROFILE=1; then each scope synchronises the
+// current stream on entry and exit and accumulates host wall time per name.
+struct Profiler {
+  static bool enabled() {
+    static int e = -1;
+    if (e < 0) {
+      const char* v = std::getenv("TTSDP_PROFILE");
+      e = (v && v[0] == '1') ? 1 : 0;
+    }
+    return e == 1;
+  }
+  static std::vector<std::pair<std::string, double>>& table() {
+    static std::vector<std::pair<std::string, double>> t;
+    return t;
+  }
+  static void add(const char* name, double s) {
+    for (auto& p : table())
+      if (p.first == name) {
+        p.second += s;
+        return;
+      }
+    table().emplace_back(name, s);
+  }
+};
+
+struct ProfScope {
+  const char* name;
+  double t0 = 0.0;
+  static double now() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return ts.tv_sec + 1e-9 * ts.tv_nsec;
+  }
+  explicit ProfScope(const char* n) : name(n) {
+    if (Profiler::enabled()) {
+      cudaStreamSynchronize(cur_stream());
+      t0 = now();
+    }
+  }
+  ~ProfScope() {
+    if (Profiler::enabled()) {
+      cudaStreamSynchronize(cur_stream());
+      Profiler::add(name, now() - t0);
+    }
+  }
+};
 
 }  // namespace ttsdp

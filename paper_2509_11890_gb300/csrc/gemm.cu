@@ -11,49 +11,84 @@ namespace ttsdp {
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int KTAB = 2048;  // K offsets precomputed once per CTA up to this length
 
-__device__ __forceinline__ long long offset_of(long long l, const IdxN& idx, const StrN& st) {
-  long long off = 0;
+// device copy of a combined index with 32-bit extents / strides
+struct Idx32 {
+  int nsub;
+  int ext[kMaxSub];
+  int s0[kMaxSub], s1[kMaxSub];
+};
+struct Gemm32 {
+  Idx32 M, N, K, B;   // M: (aM, cM), N: (bN, cN), K: (aK, bK)
+  int bA[kMaxSub], bB[kMaxSub], bC[kMaxSub];
+};
+
+__device__ __forceinline__ void offsets_of(int l, const Idx32& idx, int& o0, int& o1) {
+  o0 = 0;
+  o1 = 0;
 #pragma unroll
   for (int i = kMaxSub - 1; i >= 0; --i) {
     if (i < idx.nsub) {
-      long long e = idx.ext[i];
-      long long dgt = l % e;
+      const int e = idx.ext[i];
+      const int dgt = l % e;
       l /= e;
-      off += dgt * st.s[i];
+      o0 += dgt * idx.s0[i];
+      o1 += dgt * idx.s1[i];
     }
   }
-  return off;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) gemm_nd_kernel(GemmND g, const T* __restrict__ A,
+__global__ void __launch_bounds__(NT) gemm_nd_kernel(Gemm32 g, const T* __restrict__ A,
                                                      const T* __restrict__ B, T* __restrict__ C,
-                                                     T alpha, T beta, long long Mt, long long Nt,
-                                                     long long Kt) {
+                                                     T alpha, T beta, int Mt, int Nt, int Kt) {
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
-  __shared__ long long offAM[BM], offCM[BM], offBN[BN], offCN[BN];
-  __shared__ long long offAK[BK], offBK[BK];
+  __shared__ int offAM[BM], offCM[BM], offBN[BN], offCN[BN];
+  __shared__ int offAK[KTAB], offBK[KTAB];
 
-  const long long m0 = (long long)blockIdx.y * BM;
-  const long long n0 = (long long)blockIdx.x * BN;
-  const long long b = blockIdx.z;
+  const int m0 = blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;
   const int tid = threadIdx.x;
 
-  const long long baseA = offset_of(b, g.B, g.aB);
-  const long long baseB = offset_of(b, g.B, g.bB);
-  const long long baseC = offset_of(b, g.B, g.cB);
-
+  int baseA = 0, baseB = 0, baseC = 0;
+  {
+    int l = blockIdx.z;
+#pragma unroll
+    for (int i = kMaxSub - 1; i >= 0; --i) {
+      if (i < g.B.nsub) {
+        const int e = g.B.ext[i];
+        const int dgt = l % e;
+        l /= e;
+        baseA += dgt * g.bA[i];
+        baseB += dgt * g.bB[i];
+        baseC += dgt * g.bC[i];
+      }
+    }
+  }
   if (tid < BM) {
-    long long m = m0 + tid;
-    offAM[tid] = m < Mt ? offset_of(m, g.M, g.aM) : -1;
-    offCM[tid] = m < Mt ? offset_of(m, g.M, g.cM) : -1;
+    const int m = m0 + tid;
+    int oa = -1, oc = -1;
+    if (m < Mt) offsets_of(m, g.M, oa, oc);
+    offAM[tid] = oa;
+    offCM[tid] = oc;
   } else if (tid < BM + BN) {
-    int t = tid - BM;
-    long long n = n0 + t;
-    offBN[t] = n < Nt ? offset_of(n, g.N, g.bN) : -1;
-    offCN[t] = n < Nt ? offset_of(n, g.N, g.cN) : -1;
+    const int t = tid - BM;
+    const int n = n0 + t;
+    int ob = -1, oc = -1;
+    if (n < Nt) offsets_of(n, g.N, ob, oc);
+    offBN[t] = ob;
+    offCN[t] = oc;
+  }
+  const bool ktab = Kt <= KTAB;
+  if (ktab) {
+    for (int k = tid; k < Kt; k += NT) {
+      int oa, ob;
+      offsets_of(k, g.K, oa, ob);
+      offAK[k] = oa;
+      offBK[k] = ob;
+    }
   }
 
   const int tx = tid % 16, ty = tid / 16;
@@ -63,32 +98,32 @@ __global__ void __launch_bounds__(NT) gemm_nd_kernel(GemmND g, const T* __restri
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
-  for (long long k0 = 0; k0 < Kt; k0 += BK) {
+  for (int k0 = 0; k0 < Kt; k0 += BK) {
     __syncthreads();
-    if (tid < BK) {
-      long long k = k0 + tid;
-      offAK[tid] = k < Kt ? offset_of(k, g.K, g.aK) : -1;
-    } else if (tid < 2 * BK) {
-      int t = tid - BK;
-      long long k = k0 + t;
-      offBK[t] = k < Kt ? offset_of(k, g.K, g.bK) : -1;
+    if (!ktab && tid < BK) {
+      const int k = k0 + tid;
+      int oa = -1, ob = -1;
+      if (k < Kt) offsets_of(k, g.K, oa, ob);
+      offAK[tid] = oa;
+      offBK[tid] = ob;
     }
     __syncthreads();
-    // A tile: BM x BK elements, k fastest across threads
+    const int kb = ktab ? k0 : 0;
 #pragma unroll
     for (int r = 0; r < (BM * BK) / NT; ++r) {
-      int e = tid + r * NT;
-      int kk = e % BK, mm = e / BK;
-      long long om = offAM[mm], ok = offAK[kk];
-      As[kk][mm] = (om >= 0 && ok >= 0) ? A[baseA + om + ok] : T(0);
+      const int e = tid + r * NT;
+      const int kk = e % BK, mm = e / BK;
+      const int om = offAM[mm];
+      const bool kin = k0 + kk < Kt;
+      As[kk][mm] = (om >= 0 && kin) ? A[baseA + om + offAK[kb + kk]] : T(0);
     }
-    // B tile: BK x BN elements, n fastest across threads
 #pragma unroll
     for (int r = 0; r < (BN * BK) / NT; ++r) {
-      int e = tid + r * NT;
-      int nn = e % BN, kk = e / BN;
-      long long on = offBN[nn], ok = offBK[kk];
-      Bs[kk][nn] = (on >= 0 && ok >= 0) ? B[baseB + ok + on] : T(0);
+      const int e = tid + r * NT;
+      const int nn = e % BN, kk = e / BN;
+      const int on = offBN[nn];
+      const bool kin = k0 + kk < Kt;
+      Bs[kk][nn] = (on >= 0 && kin) ? B[baseB + offBK[kb + kk] + on] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -107,11 +142,11 @@ __global__ void __launch_bounds__(NT) gemm_nd_kernel(GemmND g, const T* __restri
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    long long om = offCM[ty + 16 * i];
+    const int om = offCM[ty + 16 * i];
     if (om < 0) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      long long on = offCN[tx + 16 * j];
+      const int on = offCN[tx + 16 * j];
       if (on < 0) continue;
       T* c = C + baseC + om + on;
       T v = alpha * acc[i][j];
@@ -119,6 +154,17 @@ __global__ void __launch_bounds__(NT) gemm_nd_kernel(GemmND g, const T* __restri
       *c = v;
     }
   }
+}
+
+Idx32 to32(const IdxN& idx, const StrN& a, const StrN& b) {
+  Idx32 o;
+  o.nsub = idx.nsub;
+  for (int i = 0; i < kMaxSub; ++i) {
+    o.ext[i] = idx.ext[i];
+    o.s0[i] = (int)a.s[i];
+    o.s1[i] = (int)b.s[i];
+  }
+  return o;
 }
 
 }  // namespace
@@ -136,8 +182,23 @@ void gemm_nd(const GemmND& g, const T* A, size_t nA, const T* B, size_t nB, T* C
            "gemm_nd: operand extent exceeds its buffer");
   TT_CHECK(Bt <= 65535, TT_E_SHAPE, "gemm_nd: batch too large");
   TT_CHECK((Mt + BM - 1) / BM < 65536, TT_E_SHAPE, "gemm_nd: M too large");
+  // offsets are 32-bit on the device
+  const long long lim = 2147483647LL;
+  TT_CHECK(ra < lim && rb < lim && rc < lim && Mt < lim && Nt < lim && Kt < lim, TT_E_SHAPE,
+           "gemm_nd: operand too large for 32-bit offsets");
+  Gemm32 d;
+  d.M = to32(g.M, g.aM, g.cM);
+  d.N = to32(g.N, g.bN, g.cN);
+  d.K = to32(g.K, g.aK, g.bK);
+  d.B.nsub = g.B.nsub;
+  for (int i = 0; i < kMaxSub; ++i) {
+    d.B.ext[i] = g.B.ext[i];
+    d.bA[i] = (int)g.aB.s[i];
+    d.bB[i] = (int)g.bB.s[i];
+    d.bC[i] = (int)g.cB.s[i];
+  }
   dim3 grid((unsigned)((Nt + BN - 1) / BN), (unsigned)((Mt + BM - 1) / BM), (unsigned)Bt);
-  gemm_nd_kernel<T><<<grid, NT, 0, st>>>(g, A, B, C, alpha, beta, Mt, Nt, Kt);
+  gemm_nd_kernel<T><<<grid, NT, 0, st>>>(d, A, B, C, alpha, beta, (int)Mt, (int)Nt, (int)Kt);
   count_launch();
   check_launch("gemm_nd_kernel");
 }

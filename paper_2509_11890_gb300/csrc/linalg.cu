@@ -146,6 +146,19 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
   }
   __syncthreads();
   const T tol = T(8) * eps_of<T>();
+  // columns whose squared norm is below (eps ||A||_F)^2 are numerical noise:
+  // rotating against them cannot change any singular value above that level
+  // and would keep the sweep from terminating on rank-deficient inputs
+  __shared__ T s_floor;
+  {
+    __shared__ T red[kWarps];
+    T loc = T(0);
+    for (long long idx = tid; idx < (long long)m * n; idx += kThreads) loc += Wc[idx] * Wc[idx];
+    T fro2 = block_sum(loc, red);
+    if (tid == 0) s_floor = eps_of<T>() * eps_of<T>() * fro2;
+    __syncthreads();
+  }
+  const T floor2 = s_floor;
   const int nn = n + (n & 1);
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) s_rot = 0;
@@ -168,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
         a = warp_sum(a);
         b = warp_sum(b);
         g = warp_sum(g);
-        if (g != T(0) && fabs(g) > tol * sqrt(a * b)) {
+        if (g != T(0) && a > floor2 && b > floor2 && fabs(g) > tol * sqrt(a * b)) {
           T zeta = (b - a) / (T(2) * g);
           T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           T c = T(1) / sqrt(T(1) + t * t);
@@ -410,6 +423,25 @@ void qr_thin(MatView<T> A, T* Q, T* R, cudaStream_t st) {
 template <typename T>
 void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st) {
   if (A.m == 0 || A.n == 0) return;
+  // strongly rectangular: reduce to the square triangular factor first so the
+  // Jacobi sweeps run over min(m, n) rows instead of max(m, n)
+  if (A.m >= 2 * A.n) {
+    const int m = A.m, n = A.n;
+    DBuf<T> Q((size_t)m * n), R((size_t)n * n), UR((size_t)n * n);
+    qr_thin<T>(A, Q.get(), R.get(), st);
+    svd_thin<T>(MatView<T>{R.get(), n, n, n, 1}, UR.get(), S, Vt, st);
+    gemm_rm<T>(false, false, m, n, n, T(1), Q.get(), n, 0, UR.get(), n, 0, T(0), U, n, 0, 1, st);
+    return;
+  }
+  if (A.n >= 2 * A.m) {
+    // A^T = Q R  =>  A = R^T Q^T ; R^T = U S Vr^T  =>  Vt = Vr^T Q^T
+    const int m = A.m, n = A.n;
+    DBuf<T> Q((size_t)n * m), R((size_t)m * m), VR((size_t)m * m);
+    qr_thin<T>(MatView<T>{A.p, n, m, A.cs, A.rs}, Q.get(), R.get(), st);
+    svd_thin<T>(MatView<T>{R.get(), m, m, 1, m}, U, S, VR.get(), st);
+    gemm_rm<T>(false, true, m, n, m, T(1), VR.get(), m, 0, Q.get(), m, 0, T(0), Vt, n, 0, 1, st);
+    return;
+  }
   bool tr = A.m < A.n;
   int m = tr ? A.n : A.m, n = tr ? A.m : A.n;
   DBuf<T> Wc((size_t)m * n), Vc((size_t)n * n);

@@ -6,7 +6,9 @@
 // dense local operators and solved by LU; the block index is moved by a
 // truncated SVD with a random kick; rounding uses the spectral shift of
 // Corollary psdness_rounding.
+#include <algorithm>
 #include <cmath>
+#include <functional>
 #include <limits>
 
 #include "contract.cuh"
@@ -147,10 +149,90 @@ BlockTT init_block(int d, int nblk, int rk, Counter& rnd) {
 struct AmenInfo {
   int sweeps = 0;
   double max_change = 0.0;
+  long long gmres_iters = 0;
 };
 
+// Restarted GMRES (Saad & Schultz) on device vectors with classical
+// Gram-Schmidt applied twice and Givens rotations on the host-side Hessenberg
+// matrix. Stops at ||b - A x|| <= tol ||b|| or after maxit products. Returns
+// the number of operator products.
+int gmres(size_t N, const std::function<void(const double*, double*)>& A, const double* b, double* x, double tol,
+          int m, int maxit) {
+  cudaStream_t st = cur_stream();
+  const double bnorm = dev_norm(b, N);
+  if (bnorm == 0.0) {
+    dev_fill(x, N, 0.0, st);
+    return 0;
+  }
+  DBuf<double> V((size_t)(m + 1) * N), w(N), hdev(m + 1);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
+  int total = 0;
+  while (total < maxit) {
+    A(x, w.get());
+    dev_scale(w.get(), N, -1.0, st);
+    dev_axpy(w.get(), b, N, 1.0, st);
+    const double beta = dev_norm(w.get(), N);
+    if (beta <= tol * bnorm) break;
+    dev_copy(V.get(), w.get(), N, st);
+    dev_scale(V.get(), N, 1.0 / beta, st);
+    std::fill(g.begin(), g.end(), 0.0);
+    std::fill(H.begin(), H.end(), 0.0);
+    g[0] = beta;
+    int jl = -1;
+    bool done = false;
+    for (int j = 0; j < m && total < maxit; ++j) {
+      A(V.get() + (size_t)j * N, w.get());
+      ++total;
+      for (int pass = 0; pass < 2; ++pass) {
+        dev_multi_dot(V.get(), j + 1, N, w.get(), hdev.get(), st);
+        std::vector<double> h(j + 1);
+        TT_CUDA(cudaMemcpyAsync(h.data(), hdev.get(), (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TT_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
+        gemm_rm<double>(true, false, (int)N, 1, j + 1, -1.0, V.get(), (int)N, 0, hdev.get(), 1, 0, 1.0, w.get(), 1, 0,
+                        1, st);
+      }
+      const double hn = dev_norm(w.get(), N);
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) {
+        dev_copy(V.get() + (size_t)(j + 1) * N, w.get(), N, st);
+        dev_scale(V.get() + (size_t)(j + 1) * N, N, 1.0 / hn, st);
+      }
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      const double rr = std::hypot(a, c);
+      cs[j] = rr > 0 ? a / rr : 1.0;
+      sn[j] = rr > 0 ? c / rr : 0.0;
+      H[(size_t)j * m + j] = rr;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      jl = j;
+      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) {
+        done = true;
+        break;
+      }
+    }
+    if (jl < 0) break;
+    std::vector<double> y(jl + 1, 0.0);
+    for (int i = jl; i >= 0; --i) {
+      double s = g[i];
+      for (int t2 = i + 1; t2 <= jl; ++t2) s -= H[(size_t)i * m + t2] * y[t2];
+      y[i] = H[(size_t)i * m + i] != 0.0 ? s / H[(size_t)i * m + i] : 0.0;
+    }
+    upload(hdev.get(), y);
+    gemm_rm<double>(true, false, (int)N, 1, jl + 1, 1.0, V.get(), (int)N, 0, hdev.get(), 1, 0, 1.0, x, 1, 0, 1, st);
+    if (done) break;
+  }
+  return total;
+}
+
 BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap, int kick, int max_sweeps,
-                   Counter& rnd, int prec, AmenInfo* info) {
+                   Counter& rnd, int prec, int dense_max, int gmres_restart, int gmres_maxit, AmenInfo* info) {
   const int nblk = nd.nblk();
   cudaStream_t st = cur_stream();
   BlockTT w = w0 ? *w0 : init_block(d, nblk, kick, rnd);
@@ -180,7 +262,10 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
     for (auto* v : {&rp, &rdd, &rc, &rt})
       for (auto& pe : *v) fn(pe.second);
   };
-  for (int k = d - 1; k >= 1; --k) for_all([&](Env& e) { e.push_right(frame, k, prec); });
+  {
+    ProfScope ps("amen.env_init");
+    for (int k = d - 1; k >= 1; --k) for_all([&](Env& e) { e.push_right(frame, k, prec); });
+  }
 
   std::vector<int> blockshape = {frame.r[0], 4, frame.r[1]};
   int sweep = 0;
@@ -194,6 +279,57 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
       const size_t n = (size_t)rl * 4 * rr;
       const int nb = nd.ineq ? 3 : 2;
       const size_t N = nb * n;
+      const size_t rc0 = (nb - 1) * n;
+      auto nw = std::make_shared<DBuf<double>>(nblk * n);
+      if (N > (size_t)dense_max) {
+        ProfScope ps("amen.gmres_solve");
+        // matrix-free reduced system (eq. reduced_kkt_system) solved by GMRES:
+        // each block product inserts the vector into core k and contracts it
+        // with the cached environments and the operator core
+        auto apply_sum = [&](std::vector<Env>& es, const double* x, double* y, double scale, bool acc) {
+          DBuf<double> tmp(n);
+          if (!acc) dev_fill(y, n, 0.0, st);
+          for (Env& e : es) {
+            CDims c{rl, rr, e.op.r[k], e.op.r[k + 1], rl, rr, e.op.m, e.op.n};
+            local_apply(c, e.L[k].get(), e.op.core(k), e.R[k + 1].get(), x, tmp.get(), prec, st);
+            dev_axpy(y, tmp.get(), n, scale, st);
+          }
+        };
+        DBuf<double> r_p(n), r_d(n), r_c(n), b(N), x(N), t(n);
+        sum_local_rhs(rp, frame, k, r_p.get(), n, prec);
+        sum_local_rhs(rdd, frame, k, r_d.get(), n, prec);
+        sum_local_rhs(rc, frame, k, r_c.get(), n, prec);
+        dev_copy2d(b.get(), 1, r_p.get(), 1, n, 1, -1.0, st);
+        dev_copy2d(b.get() + rc0, 1, r_c.get(), 1, n, 1, -1.0, st);
+        apply_sum(eLX, r_d.get(), b.get() + rc0, 1.0, true);
+        if (nd.ineq) {
+          DBuf<double> r_t(n);
+          sum_local_rhs(rt, frame, k, r_t.get(), n, prec);
+          dev_copy2d(b.get() + n, 1, r_t.get(), 1, n, 1, -1.0, st);
+        }
+        auto matvec = [&](const double* xin, double* y) {
+          apply_sum(eA, xin, y, -1.0, false);
+          apply_sum(eK, xin + n, y, 1.0, true);
+          if (nd.ineq) {
+            apply_sum(eTA, xin, y + n, nd.sgn, false);
+            apply_sum(eDK, xin + 2 * n, y + n, 1.0, true);
+          }
+          apply_sum(eAT, xin + n, t.get(), 1.0, false);
+          if (nd.ineq) apply_sum(eAiT, xin + 2 * n, t.get(), -nd.sgn, true);
+          apply_sum(eLZ, xin, y + rc0, 1.0, false);
+          apply_sum(eLX, t.get(), y + rc0, 1.0, true);
+        };
+        // warm start from the block solution of the previous visit of this core
+        if (blockshape[0] == rl && blockshape[2] == rr && block) dev_copy(x.get(), block->get(), N, st);
+        else dev_fill(x.get(), N, 0.0, st);
+        info->gmres_iters += gmres(N, matvec, b.get(), x.get(), 0.1 * tol, gmres_restart, gmres_maxit);
+        dev_copy(nw->get(), x.get(), N, st);
+        double* dZ = nw->get() + (nblk - 1) * n;
+        apply_sum(eAT, x.get() + n, dZ, 1.0, false);
+        if (nd.ineq) apply_sum(eAiT, x.get() + 2 * n, dZ, -nd.sgn, true);
+        dev_axpy(dZ, r_d.get(), n, -1.0, st);
+      } else {
+      ProfScope ps("amen.dense_solve");
       // local operators
       DBuf<double> A(n * n), AT(n * n), Ky(n * n), LZ(n * n), LX(n * n);
       eA[0].local_mat(frame, k, A.get(), prec);
@@ -211,7 +347,6 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
       dev_copy2d(K.get(), N, A.get(), n, n, n, -1.0, st);
       dev_copy2d(K.get() + n, N, Ky.get(), n, n, n, 1.0, st);
       // last row block c: [LZ, LX AT, -sgn LX AiT]
-      const size_t rc0 = (nb - 1) * n;
       dev_copy2d(K.get() + rc0 * N, N, LZ.get(), n, n, n, 1.0, st);
       gemm_rm<double>(false, false, n, n, n, 1.0, LX.get(), n, 0, AT.get(), n, 0, 0.0, K.get() + rc0 * N + n,
                       N, 0, 1, st);
@@ -237,7 +372,6 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
       }
       lu_solve<double>((int)N, K.get(), b.get(), st);
       // assemble the new block core [dX, dY, (dT), dZ]
-      auto nw = std::make_shared<DBuf<double>>(nblk * n);
       dev_copy(nw->get(), b.get(), nb * n, st);
       double* dZ = nw->get() + (nblk - 1) * n;
       // dZ = AT dY - sgn AiT dT - r_d
@@ -246,6 +380,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         gemm_rm<double>(false, false, n, 1, n, -nd.sgn, AiT.get(), n, 0, b.get() + 2 * n, 1, 0, 1.0, dZ, 1, 0,
                         1, st);
       dev_axpy(dZ, r_d.get(), n, -1.0, st);
+      }
       // convergence measure
       double nrm = dev_norm(nw->get(), nblk * n);
       if (blockshape[0] == rl && blockshape[2] == rr && block) {
@@ -266,6 +401,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         break;
       }
       if (forward) {
+        ProfScope ps("amen.move_fwd");
         const int rows = rl * 4, cols = nblk * rr;
         DBuf<double> mat((size_t)rows * cols);
         for (int bb = 0; bb < nblk; ++bb)
@@ -308,6 +444,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         blockshape = {nk, 4, r3};
         for_all([&](Env& e) { e.push_left(frame, k, prec); });
       } else {
+        ProfScope ps("amen.move_bwd");
         const int rows = nblk * rl, cols = 4 * rr;
         int kk = std::min(rows, cols);
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
@@ -484,7 +621,10 @@ double min_gen_eig(const DTT& M, const DTT& dM, DTT* e_io, bool warm, Counter& r
       DBuf<double> Mk((size_t)nl * nl), Dk((size_t)nl * nl), x(nl);
       eM.local_mat(e, k, Mk.get(), prec);
       eD.local_mat(e, k, Dk.get(), prec);
-      lam = local_min_eig(nl, Mk.get(), Dk.get(), x.get());
+      {
+        ProfScope ps("eig.local");
+        lam = local_min_eig(nl, Mk.get(), Dk.get(), x.get());
+      }
       const bool last = forward ? (k == d - 1) : (k == 0);
       if (last) {
         auto c = std::make_shared<DBuf<double>>(nl);
@@ -733,7 +873,8 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
   }
   AmenInfo info;
   BlockTT w = amen_solve(nd, d, w_ ? w_.get() : nullptr, eta_, o_.rank_cap, o_.kick, o_.max_sweeps, rnd_,
-                         o_.prec, &info);
+                         o_.prec, o_.local_dense_max, o_.gmres_restart, o_.gmres_max_iters, &info);
+  gmres_iters_ += info.gmres_iters;
   w_ = std::make_unique<BlockTT>(w);
   *sweeps = info.sweeps;
   dX = unvec(w.component(0));
@@ -801,7 +942,11 @@ IterLog Solver::iterate() {
   TT_CUDA(cudaEventRecord(e0, st));
   IterLog log;
   log.iter = it_;
-  Measures ms = measures();
+  Measures ms;
+  {
+    ProfScope ps("ipm.measures");
+    ms = measures();
+  }
   log.mu = ms.mu;
   log.rel_p = ms.rel_p;
   log.rel_d = ms.rel_d;
@@ -822,7 +967,10 @@ IterLog Solver::iterate() {
     int sw = 0;
     direction(dir, 0.0, nullptr, nullptr, nullptr, nullptr, zp, zd, dXa, dYa, dTa, dZa, &sw);
     double apa, ada;
-    steps(dXa, dTa, dZa, &apa, &ada);
+    {
+      ProfScope ps("ipm.steps");
+      steps(dXa, dTa, dZa, &apa, &ada);
+    }
     DTT Xa = tt_add(X_, dXa, 1.0, apa), Za = tt_add(Z_, dZa, 1.0, ada);
     double mu_aff = tt_inner(vecv(Za), vecv(Xa));
     DTT dsa;
@@ -838,13 +986,17 @@ IterLog Solver::iterate() {
     direction(dir, sigma * ms.mu, &dXa, &dZa, p_.ineq ? &dTa : nullptr, p_.ineq ? &dsa : nullptr, zp, zd, dX, dY, dT,
               dZ, &sw);
     double ap, ad;
-    steps(dX, dT, dZ, &ap, &ad);
+    {
+      ProfScope ps("ipm.steps");
+      steps(dX, dT, dZ, &ap, &ad);
+    }
     log.alpha_p = ap;
     log.alpha_d = ad;
     log.direction = dir;
     log.sweeps = sw;
     log.max_rank_W = w_->frame.maxrank();
     const double tol_p = eta_ * (1.0 + nB_) / 10.0, tol_d = eta_ * (1.0 + nC_) / 10.0;
+    ProfScope ps_round("ipm.round");
     X_ = round_psd(tt_add(X_, dX, 1.0, ap), tol_p, &I_);
     Z_ = round_psd(tt_add(Z_, dZ, 1.0, ad), tol_d, &I_);
     Y_ = round_psd(tt_add(Y_, dY, 1.0, ad), tol_d, nullptr);
@@ -853,6 +1005,7 @@ IterLog Solver::iterate() {
   }
   log.max_rank_X = X_.maxrank();
   log.max_rank_Z = Z_.maxrank();
+  log.gmres_iters = gmres_iters_;
   TT_CUDA(cudaEventRecord(e1, st));
   TT_CUDA(cudaEventSynchronize(e1));
   float msec = 0.f;

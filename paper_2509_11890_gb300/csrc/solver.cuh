@@ -40,6 +40,7 @@ struct Options {
   int prec = 0;
   int max_iters = 60, max_sweeps = 4, kick = 4, eig_rank = 4, eig_sweeps = 4;
   uint64_t seed = 1234;
+  int local_dense_max = 4096, gmres_restart = 40, gmres_max_iters = 400;
 };
 
 struct IterLog {
@@ -47,6 +48,7 @@ struct IterLog {
   double mu = 0, rel_p = 0, rel_d = 0, rel_gap = 0, pobj = 0, dobj = 0, alpha_p = 0, alpha_d = 0;
   int max_rank_X = 0, max_rank_Z = 0, max_rank_W = 0;
   double seconds = 0;
+  long long gmres_iters = 0;
 };
 
 class Solver {
@@ -81,6 +83,7 @@ class Solver {
   DTT I_, X_, Y_, T_, Z_;
   double eta_, nB_, nC_;
   int it_ = 0, N_;
+  long long gmres_iters_ = 0;
   std::unique_ptr<BlockTT> w_;
   DTT eX_, eZ_, eT_, eS_;
   bool haveX_ = false, haveZ_ = false, haveT_ = false, haveS_ = false;

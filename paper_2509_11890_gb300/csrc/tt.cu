@@ -125,6 +125,41 @@ __global__ void diag_core_kernel(const double* v, int r, int m, int r2, double* 
   }
 }
 
+// out[vec_TT position] = M[row][col] for an n^d x n^d row-major matrix
+__global__ void vec_tt_perm_kernel(const double* M, int d, int n, long long N, double* out) {
+  long long tot = N * N;
+  GRID_LOOP(pos, tot) {
+    long long rem = pos, row = 0, col = 0, w = 1;
+    for (int k = d - 1; k >= 0; --k) {  // digits from least significant: (a_k, b_k) pairs
+      long long b = rem % n;
+      rem /= n;
+      long long a = rem % n;
+      rem /= n;
+      row += a * w;
+      col += b * w;
+      w *= n;
+    }
+    out[pos] = M[row * N + col];
+  }
+}
+
+// out[i] = <V_i, w> for the nvec rows V_i of a row-major nvec x N matrix; one CTA per row
+__global__ void multi_dot_kernel(const double* __restrict__ V, long long N, const double* __restrict__ w,
+                                 double* out) {
+  __shared__ double red[32];
+  const double* v = V + (long long)blockIdx.x * N;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) s += v[i] * w[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    out[blockIdx.x] = t;
+  }
+}
+
 __global__ void dot_kernel(const double* a, const double* b, long long n, double* out) {
   __shared__ double red[32];
   double s = 0.0;
@@ -179,6 +214,13 @@ void dev_scale_rows(double* a, int rows, int cols, const double* s, cudaStream_t
   count_launch();
   check_launch("scale_rows");
 }
+void dev_multi_dot(const double* V, int nvec, size_t N, const double* w, double* out, cudaStream_t st) {
+  if (nvec <= 0) return;
+  multi_dot_kernel<<<nvec, 512, 0, st>>>(V, (long long)N, w, out);
+  count_launch();
+  check_launch("multi_dot");
+}
+
 double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st) {
   DBuf<double> out(1);
   dot_kernel<<<1, 1024, 0, st>>>(a, b, (long long)n, out.get());
@@ -445,6 +487,51 @@ DTT tt_orth_right(const DTT& a) {
     t.c[k - 1] = pc;
     t.r[k] = kk;
   }
+  return t;
+}
+
+DTT tt_from_dense(const double* dense, int d, int n, double eps_rel, int cap) {
+  TT_CHECK(d >= 1 && n >= 1 && dense, TT_E_INVALID_ARG, "tt_from_dense: bad arguments");
+  cudaStream_t st = cur_stream();
+  long long N = 1;
+  for (int k = 0; k < d; ++k) N *= n;
+  const long long tot = N * N;
+  const int M = n * n;
+  auto cur = std::make_shared<DBuf<double>>((size_t)tot);
+  vec_tt_perm_kernel<<<grid1(tot), 256, 0, st>>>(dense, d, n, N, cur->get());
+  count_launch();
+  check_launch("vec_tt_perm");
+  const double nrm = std::sqrt(std::max(0.0, dev_dot(cur->get(), cur->get(), (size_t)tot, st)));
+  const double thr = eps_rel * nrm / std::sqrt((double)(d > 1 ? d - 1 : 1));
+  std::vector<int> r(d + 1, 1);
+  std::vector<std::shared_ptr<DBuf<double>>> cores(d);
+  long long rest = tot;
+  for (int k = 0; k + 1 < d; ++k) {
+    const int rows = r[k] * M;
+    rest /= M;
+    const long long cols = rest;
+    const int kk = (int)std::min<long long>(rows, cols);
+    DBuf<double> U((size_t)rows * kk), S((size_t)kk), Vt((size_t)kk * cols);
+    svd_thin<double>(MatView<double>{cur->get(), rows, (int)cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+    std::vector<double> hs(kk);
+    TT_CUDA(cudaMemcpyAsync(hs.data(), S.get(), kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(cudaStreamSynchronize(st));
+    const int keep = truncation_rank(hs, thr, cap);
+    cores[k] = std::make_shared<DBuf<double>>((size_t)rows * keep);
+    dev_copy2d(cores[k]->get(), keep, U.get(), kk, rows, keep, 1.0, st);
+    dev_scale_rows(Vt.get(), keep, (int)cols, S.get(), st);
+    auto nxt = std::make_shared<DBuf<double>>((size_t)keep * cols);
+    dev_copy(nxt->get(), Vt.get(), (size_t)keep * cols, st);
+    cur = nxt;
+    r[k + 1] = keep;
+  }
+  cores[d - 1] = cur;
+  DTT t;
+  t.d = d;
+  t.m = n;
+  t.n = n;
+  t.r = r;
+  t.c = cores;
   return t;
 }
 

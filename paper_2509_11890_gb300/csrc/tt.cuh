@@ -64,6 +64,12 @@ double tt_norm(const DTT& a);
 // Returns the rounded TT (same m, n) and zeta = sqrt(sum discarded sigma^2).
 std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap);
 
+// TT-SVD (Oseledets 2011) of a dense n^d x n^d matrix given row-major on the
+// device: the matrix is permuted to its vec_TT order (Section 3.1) and split
+// by sequential truncated SVDs with per-bond threshold eps_rel ||M||_F / sqrt(d-1)
+// and at most `cap` (<= 0: none). Returns a TT matrix with n x n modes.
+DTT tt_from_dense(const double* dense, int d, int n, double eps_rel, int cap);
+
 // right-to-left orthogonalisation (cores 1..d-1 right-orthonormal)
 DTT tt_orth_right(const DTT& a);
 
@@ -87,5 +93,7 @@ void dev_copy2d(double* dst, long long dld, const double* src, long long sld, in
                 double alpha, cudaStream_t st);
 void dev_scale_rows(double* a, int rows, int cols, const double* s, cudaStream_t st);
 double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st);
+// out[i] = <V_i, w> for the rows of a row-major nvec x N matrix (device output)
+void dev_multi_dot(const double* V, int nvec, size_t N, const double* w, double* out, cudaStream_t st);
 
 }  // namespace ttsdp

@@ -68,3 +68,37 @@ def test_cc_reaches_dense_optimum():
     res = ctx.solve()
     assert res["status"] == 0, res
     assert abs(res["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 5e-3
+
+
+def test_maxcut_gmres_local_solver_matches_dense_path():
+    # forcing every local system onto the matrix-free GMRES path gives the same optimum
+    d = 4
+    inst = inputs.maxcut_kron(d, 2)
+    ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]))
+    ctx = tg.Context.maxcut(inst["adjacency_cores"], _opts(local_dense_max=0))
+    res = ctx.solve()
+    assert res["status"] == 0, res
+    assert abs(res["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3
+    info = ctx.newton_step()
+    assert info["gmres_iters"] > 0
+
+
+@pytest.mark.parametrize("prec", [tg.FP32])
+def test_maxcut_mixed_precision_reaches_optimum(prec):
+    d = 4
+    inst = inputs.maxcut_kron(d, 2)
+    ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]))
+    ctx = tg.Context.maxcut(inst["adjacency_cores"], _opts(precision=prec))
+    res = ctx.solve()
+    assert res["status"] == 0, res
+    assert abs(res["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3
+
+
+def test_tt_from_dense_matches_oracle_tt_svd():
+    d = 6
+    inst = inputs.maxcut_kron_er(d, 0)
+    w = inst["weights"]
+    cores = tg.tt_from_dense(torch.from_numpy(w).cuda(), eps_rel=1e-13)
+    np.testing.assert_allclose(tt.full_mat(cores), w, atol=1e-10)
+    ref = tp.graph_tt(w, eps_rel=1e-13)
+    assert tt.ranks(cores) == tt.ranks(ref)
