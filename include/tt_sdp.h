@@ -97,6 +97,23 @@ tt_status tt_local_apply(const tt_contract_dims* dims, const double* phi, const 
                          const double* psi, const double* x, double* y, int32_t precision,
                          void* stream);
 
+/* Allocation-free variant of tt_env_left_step (FP64 only). The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory while
+ * they run, such as a host framework whose own allocator owns the device heap
+ * or a latency-critical loop that must not pay for allocation. Instead of
+ * stream-ordered scratch, the two intermediate tensors live in one fixed
+ * file-scope device array of 4,194,304 doubles (32 MiB) that every GPU loading
+ * the library holds until the process exits. Shapes whose intermediates
+ * (rw*R*n*rv2 + rw*m*R2*rv2 doubles) exceed it are rejected with TT_E_NOMEM
+ * before anything runs. The first call on a device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture. All calls share the array and it keeps the last call's contents
+ * (every element a call reads it has written itself first, so nothing needs
+ * clearing); calls that overlap on the GPU, on different streams or devices
+ * sharing a context, race on it. Arguments as for tt_env_left_step. */
+tt_status tt_env_left_step_noalloc(const tt_contract_dims* dims, const double* phi, const double* u,
+                                   const double* op, const double* v, double* out, void* stream);
+
 /* Dense projected operator W^T Op W at one core: out[(a',i,b')][(a,j,b)],
  * (rw*m*rw2) x (rv*n*rv2) row-major doubles. */
 tt_status tt_local_matrix(const tt_contract_dims* dims, const double* phi, const double* op,

@@ -57,6 +57,8 @@ SIGNATURES = {
                                    c_int32, c_void_p]),
     "tt_env_right_step": (c_int32, [ctypes.POINTER(ContractDims), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_int32, c_void_p]),
+    "tt_env_left_step_noalloc": (c_int32, [ctypes.POINTER(ContractDims), c_void_p, c_void_p, c_void_p, c_void_p,
+                                           c_void_p, c_void_p]),
     "tt_local_apply": (c_int32, [ctypes.POINTER(ContractDims), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_int32, c_void_p]),
     "tt_local_matrix": (c_int32, [ctypes.POINTER(ContractDims), c_void_p, c_void_p, c_void_p, c_void_p, c_int32,

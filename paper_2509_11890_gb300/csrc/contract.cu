@@ -380,3 +380,70 @@ void stats_reset() {
 }
 
 }  // namespace ttsdp
+
+// ---------------------------------------------------------------------------
+// Allocation-free left environment update.
+//
+// Some callers cannot allocate device memory while they run: a host
+// framework that owns the whole device heap through its own allocator (a
+// raw cudaMalloc would bypass its accounting and could fail once the heap is
+// handed out), or a latency-critical loop that must not pay for an
+// allocation or the device-wide synchronisation cudaFree can imply. For them
+// this entry point runs the FP64 left environment update with its two
+// intermediate tensors in a fixed file-scope device array instead of
+// stream-ordered scratch. The array is created when the library is loaded
+// and every device that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------
+namespace ttsdp {
+namespace {
+
+constexpr size_t kNoAllocScratch = size_t(1) << 22;  // doubles (32 MiB)
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+// Host code cannot use g_noalloc_scratch's name as a device address; the
+// address is looked up once per device, with that device current.
+double* noalloc_scratch_ptr() {
+  static std::mutex mu;
+  static double* ptrs[64] = {nullptr};
+  int dev = 0;
+  TT_CUDA(cudaGetDevice(&dev));
+  TT_CHECK(dev >= 0 && dev < 64, TT_E_CUDA, "device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      throw TTError(TT_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    ptrs[dev] = static_cast<double*>(p);
+  }
+  return ptrs[dev];
+}
+
+}  // namespace
+
+}  // namespace ttsdp
+
+extern "C" tt_status tt_env_left_step_noalloc(const tt_contract_dims* dims, const double* phi, const double* u,
+                                              const double* op, const double* v, double* out, void* stream) {
+  using namespace ttsdp;
+  try {
+    TT_CHECK(dims && phi && u && op && v && out, TT_E_INVALID_ARG, "null argument");
+    TT_CHECK(dims->rw > 0 && dims->rw2 > 0 && dims->R > 0 && dims->R2 > 0 && dims->rv > 0 && dims->rv2 > 0 &&
+                 dims->m > 0 && dims->n > 0,
+             TT_E_SHAPE, "dimensions must be positive");
+    const CDims d{dims->rw, dims->rw2, dims->R, dims->R2, dims->rv, dims->rv2, dims->m, dims->n};
+    const size_t t1n = (size_t)d.rw * d.R * d.n * d.rv2, t2n = (size_t)d.rw * d.m * d.R2 * d.rv2;
+    if (t1n + t2n > kNoAllocScratch)
+      return TT_E_NOMEM;  // intermediates exceed the fixed scratch (see tt_sdp.h)
+    double* s = noalloc_scratch_ptr();
+    // both intermediates are written in full before they are read, so the
+    // previous call's contents need no clearing
+    env_left_t<double>(d, phi, u, op, v, out, s, s + t1n, (cudaStream_t)stream, TT_FP64);
+    return TT_OK;
+  } catch (const TTError& e) {
+    return e.status;
+  } catch (...) {
+    return TT_E_INTERNAL;
+  }
+}
+
