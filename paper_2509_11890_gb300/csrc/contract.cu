@@ -46,6 +46,9 @@ void to_double(const float* a, double* b, long long n, cudaStream_t st) {
   check_launch("to_double");
 }
 
+void to_f32(const double* a, float* b, size_t n, cudaStream_t st) { to_float(a, b, (long long)n, st); }
+void to_f64(const float* a, double* b, size_t n, cudaStream_t st) { to_double(a, b, (long long)n, st); }
+
 double contract_flops(const CDims& d) {
   double s1 = 2.0 * d.rw * d.R * d.rv * d.n * d.rv2;
   double s2 = 2.0 * d.rw * d.rv2 * (double)(d.R * d.n) * (double)(d.m * d.R2);
@@ -73,8 +76,10 @@ static void env_left_t(const CDims& d, const T* phi, const T* u, const T* op, co
     set_batch(g, {});
     gemm_nd<T>(g, phi, nphi, v, nv, t1, nt1, T(1), T(0), st);
   }
-  // stage 2: T2[a'][i][q][b] = sum_{p,j} Op[p][i][j][q] T1[a'][p][j][b]
-  if (!tc_stage2<T>(prec, rw, R, R2, m, n, rv2, op, t1, t2, st)) {
+  // stage 2: T2[a'][i][q][b] = sum_{p,j} Op[p][i][j][q] T1[a'][p][j][b]; on the
+  // tensor cores T2 comes back as [(i,q)][(a',b)] and stage 3 reads it so
+  const bool tc = tc_stage2<T>(prec, rw, R, R2, m, n, rv2, op, t1, t2, st);
+  if (!tc) {
     GemmND g;
     set_batch(g, {{(int)rw, 0, R * n * rv2, m * R2 * rv2}});
     set_dim(g.M, g.aM, g.cM, {{(int)m, n * R2, R2 * rv2}, {(int)R2, 1, rv2}});
@@ -83,7 +88,15 @@ static void env_left_t(const CDims& d, const T* phi, const T* u, const T* op, co
     gemm_nd<T>(g, op, nop, t1, nt1, t2, nt2, T(1), T(0), st);
   }
   // stage 3: out[b'][q][b] = sum_{a',i} U[a'][i][b'] T2[a'][i][q][b]
-  {
+  if (tc) {
+    const long long nc = rw * rv2;  // row stride of the [(i,q)][(a',b)] layout
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)rw2, 1, R2 * rv2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)R2, nc, rv2}, {(int)rv2, 1, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)rw, m * rw2, rv2}, {(int)m, rw2, R2 * nc}});
+    set_batch(g, {});
+    gemm_nd<T>(g, u, nu, t2, nt2, out, nout, T(1), T(0), st);
+  } else {
     GemmND g;
     set_dim(g.M, g.aM, g.cM, {{(int)rw2, 1, R2 * rv2}});
     set_dim(g.N, g.bN, g.cN, {{(int)(R2 * rv2), 1, 1}});
@@ -144,7 +157,8 @@ static void apply_t(const CDims& d, const T* phi, const T* op, const T* psi, con
     set_batch(g, {});
     gemm_nd<T>(g, phi, nphi, x, nx, t1, nt1, T(1), T(0), st);
   }
-  if (!tc_stage2<T>(prec, rw, R, R2, m, n, rv2, op, t1, t2, st)) {
+  const bool tc = tc_stage2<T>(prec, rw, R, R2, m, n, rv2, op, t1, t2, st);
+  if (!tc) {
     GemmND g;
     set_batch(g, {{(int)rw, 0, R * n * rv2, m * R2 * rv2}});
     set_dim(g.M, g.aM, g.cM, {{(int)m, n * R2, R2 * rv2}, {(int)R2, 1, rv2}});
@@ -153,7 +167,15 @@ static void apply_t(const CDims& d, const T* phi, const T* op, const T* psi, con
     gemm_nd<T>(g, op, nop, t1, nt1, t2, nt2, T(1), T(0), st);
   }
   // stage 3: y[a'][i][b'] = sum_{q,b} T2[a'][i][q][b] Psi[b'][q][b]
-  {
+  if (tc) {
+    const long long nc = rw * rv2;
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)rw, rv2, m * rw2}, {(int)m, R2 * nc, rw2}});
+    set_dim(g.N, g.bN, g.cN, {{(int)rw2, R2 * rv2, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)R2, nc, rv2}, {(int)rv2, 1, 1}});
+    set_batch(g, {});
+    gemm_nd<T>(g, t2, nt2, psi, npsi, y, ny, T(1), T(0), st);
+  } else {
     GemmND g;
     set_dim(g.M, g.aM, g.cM, {{(int)(rw * m), R2 * rv2, rw2}});
     set_dim(g.N, g.bN, g.cN, {{(int)rw2, R2 * rv2, 1}});

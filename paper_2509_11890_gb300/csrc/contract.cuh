@@ -25,6 +25,10 @@ void local_apply(const CDims& d, const double* phi, const double* op, const doub
 void local_matrix(const CDims& d, const double* phi, const double* op, const double* psi,
                   double* out, int prec, cudaStream_t st);
 
+// FP64 <-> FP32 conversion of n contiguous elements.
+void to_f32(const double* a, float* b, size_t n, cudaStream_t st);
+void to_f64(const float* a, double* b, size_t n, cudaStream_t st);
+
 // Contraction statistics (device time via CUDA events and algorithmic flops).
 void stats_begin(cudaStream_t st);
 void stats_end(cudaStream_t st, double flops);

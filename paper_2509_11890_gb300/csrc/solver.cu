@@ -125,6 +125,55 @@ int truncation_rank_rel(const std::vector<double>& s, double tol_rel, int cap) {
 }
 
 // ---------------------------------------------------------------------------
+// precision-dispatched dense kernels of the AMEn step
+// ---------------------------------------------------------------------------
+// Thin SVD of a row-major matrix; the mixed precisions run the Jacobi sweeps
+// in FP32 (the block-index move only needs the truncation-level spectrum).
+void svd_prec(int prec, MatView<double> A, double* U, double* S, double* Vt, cudaStream_t st) {
+  if (prec == TT_FP64) {
+    svd_thin<double>(A, U, S, Vt, st);
+    return;
+  }
+  const int m = A.m, n = A.n, k = m < n ? m : n;
+  DBuf<float> a((size_t)m * n), u((size_t)m * k), s(k), vt((size_t)k * n);
+  DBuf<double> dense((size_t)m * n);
+  dev_copy2d(dense.get(), n, A.p, A.rs, m, n, 1.0, st);  // A is row-major here (cs == 1)
+  to_f32(dense.get(), a.get(), (size_t)m * n, st);
+  svd_thin<float>(MatView<float>{a.get(), m, n, n, 1}, u.get(), s.get(), vt.get(), st);
+  to_f64(u.get(), U, (size_t)m * k, st);
+  to_f64(s.get(), S, k, st);
+  to_f64(vt.get(), Vt, (size_t)k * n, st);
+}
+
+// Dense local solve K x = b (K destroyed, b becomes x). The mixed precisions
+// factor in FP32 and refine the solution twice against the FP64 residual.
+void lu_solve_prec(int prec, int N, double* K, double* b) {
+  cudaStream_t st = cur_stream();
+  if (prec == TT_FP64) {
+    lu_solve<double>(N, K, b, st);
+    return;
+  }
+  const size_t nn = (size_t)N * N;
+  DBuf<float> kf(nn), rf(N);
+  DBuf<double> x(N), r(N);
+  dev_fill(x.get(), N, 0.0, st);
+  dev_copy(r.get(), b, N, st);
+  for (int it = 0; it < 3; ++it) {
+    to_f32(K, kf.get(), nn, st);
+    to_f32(r.get(), rf.get(), N, st);
+    lu_solve<float>(N, kf.get(), rf.get(), st);
+    DBuf<double> dx(N);
+    to_f64(rf.get(), dx.get(), N, st);
+    dev_axpy(x.get(), dx.get(), N, 1.0, st);
+    if (it == 2) break;
+    // r = b - K x in FP64
+    dev_copy(r.get(), b, N, st);
+    gemm_rm<double>(false, false, N, 1, N, -1.0, K, N, 0, x.get(), 1, 0, 1.0, r.get(), 1, 0, 1, st);
+  }
+  dev_copy(b, x.get(), N, st);
+}
+
+// ---------------------------------------------------------------------------
 // block-AMEn
 // ---------------------------------------------------------------------------
 BlockTT init_block(int d, int nblk, int rk, Counter& rnd) {
@@ -370,7 +419,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
                         K.get() + rc0 * N + 2 * n, N, 0, 1, st);
         dev_copy2d(b.get() + n, 1, r_t.get(), 1, n, 1, -1.0, st);
       }
-      lu_solve<double>((int)N, K.get(), b.get(), st);
+      lu_solve_prec(prec, (int)N, K.get(), b.get());
       // assemble the new block core [dX, dY, (dT), dZ]
       dev_copy(nw->get(), b.get(), nb * n, st);
       double* dZ = nw->get() + (nblk - 1) * n;
@@ -408,7 +457,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
           dev_copy2d(mat.get() + bb * rr, cols, nw->get() + bb * n, rr, rows, rr, 1.0, st);
         int kk = std::min(rows, cols);
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
-        svd_thin<double>(MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+        svd_prec(prec, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
         std::vector<double> hs = host_copy(S.get(), kk);
         int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(rows - keep, std::max(cap - keep, 0)));
@@ -448,7 +497,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         const int rows = nblk * rl, cols = 4 * rr;
         int kk = std::min(rows, cols);
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
-        svd_thin<double>(MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+        svd_prec(prec, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
         std::vector<double> hs = host_copy(S.get(), kk);
         int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(cols - keep, std::max(cap - keep, 0)));

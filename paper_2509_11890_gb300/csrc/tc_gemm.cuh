@@ -21,4 +21,8 @@ bool tc_stage2(int prec, long long rw, long long R, long long R2, long long m, l
 void tc_gemm_tn(int prec, int M, int N, int K, int batch, const void* A, long long sA,
                 const void* B, long long sB, float* C, long long sC, cudaStream_t st);
 
+// Reads (and with reset clears) the error word a tensor-core kernel sets when
+// one of its bounded waits gives up; 0 means no failure.
+int tc_check_error(bool reset);
+
 }  // namespace ttsdp
