@@ -284,6 +284,10 @@ uint64_t tt_launch_count(void);
  * their algorithmic flop count (for the contraction TFLOP/s metric). */
 void tt_contraction_stats(double* flops, double* seconds);
 void tt_contraction_stats_reset(void);
+/* Tensor-core GEMM launches of the TF32 / BF16 contractions since the last
+ * reset: algorithmic flops (2 M N K with the unpadded K), device seconds from
+ * CUDA events around each launch, and the launch count. */
+void tt_tc_stats(double* flops, double* seconds, uint64_t* launches);
 /* Per-phase host wall time accumulated while the environment variable
  * TTSDP_PROFILE=1 is set (each phase then synchronises the stream): one
  * "name seconds" line per phase, written NUL-terminated into buf (at most cap

@@ -302,6 +302,13 @@ def contraction_stats():
     return f.value, s.value
 
 
+def tc_stats():
+    """(flops, seconds, launches) of the tensor-core GEMM launches since the last reset."""
+    f, s, n = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_uint64(0)
+    lib().tt_tc_stats(ctypes.byref(f), ctypes.byref(s), ctypes.byref(n))
+    return f.value, s.value, n.value
+
+
 def contraction_stats_reset():
     lib().tt_contraction_stats_reset()
 

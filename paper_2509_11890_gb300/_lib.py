@@ -90,6 +90,7 @@ SIGNATURES = {
     "tt_contraction_stats": (None, [P_double, P_double]),
     "tt_contraction_stats_reset": (None, []),
     "tt_profile_report": (c_size_t, [ctypes.c_char_p, c_size_t]),
+    "tt_tc_stats": (None, [P_double, P_double, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 _LIB = None

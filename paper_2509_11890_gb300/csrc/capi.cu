@@ -156,6 +156,18 @@ void tt_contraction_stats_reset(void) {
   }
 }
 
+void tt_tc_stats(double* flops, double* seconds, uint64_t* launches) {
+  try {
+    unsigned long long c = 0;
+    stats_read(flops, seconds, 1, &c);
+    if (launches) *launches = c;
+  } catch (...) {
+    if (flops) *flops = 0;
+    if (seconds) *seconds = 0;
+    if (launches) *launches = 0;
+  }
+}
+
 size_t tt_core_count(int32_t d, const int32_t* ranks, int32_t m, int32_t n) {
   if (d <= 0 || !ranks) return 0;
   size_t s = 0;

@@ -333,19 +333,27 @@ struct Stats {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
   double flops = 0.0, seconds = 0.0;
-  bool enabled = true;
-  cudaEvent_t open = nullptr;
+  unsigned long long calls = 0;
 };
-Stats& stats() {
-  static Stats s;
-  return s;
+Stats& stats(int key) {
+  static Stats s[2];
+  return s[key & 1];
+}
+void resolve(Stats& s) {
+  for (auto& ev : s.pending) {
+    TT_CUDA(cudaEventSynchronize(ev.second));
+    float ms = 0.f;
+    TT_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
+    s.seconds += ms * 1e-3;
+    s.pool.push_back(ev);
+  }
+  s.pending.clear();
 }
 }  // namespace
 
-void stats_begin(cudaStream_t st) {
-  Stats& s = stats();
+void stats_begin(cudaStream_t st, int key) {
+  Stats& s = stats(key);
   std::lock_guard<std::mutex> lk(s.mu);
-  if (!s.enabled) return;
   std::pair<cudaEvent_t, cudaEvent_t> ev;
   if (!s.pool.empty()) {
     ev = s.pool.back();
@@ -358,47 +366,34 @@ void stats_begin(cudaStream_t st) {
   s.pending.push_back(ev);
 }
 
-void stats_end(cudaStream_t st, double flops) {
-  Stats& s = stats();
+void stats_end(cudaStream_t st, double flops, int key) {
+  Stats& s = stats(key);
   std::lock_guard<std::mutex> lk(s.mu);
-  if (!s.enabled || s.pending.empty()) return;
+  if (s.pending.empty()) return;
   TT_CUDA(cudaEventRecord(s.pending.back().second, st));
   s.flops += flops;
-  if (s.pending.size() > 4096) {
-    // resolve older pairs to bound the pool
-    for (auto& ev : s.pending) {
-      TT_CUDA(cudaEventSynchronize(ev.second));
-      float ms = 0.f;
-      TT_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
-      s.seconds += ms * 1e-3;
-      s.pool.push_back(ev);
-    }
-    s.pending.clear();
-  }
+  ++s.calls;
+  if (s.pending.size() > 4096) resolve(s);
 }
 
-void stats_read(double* flops, double* seconds) {
-  Stats& s = stats();
+void stats_read(double* flops, double* seconds, int key, unsigned long long* calls) {
+  Stats& s = stats(key);
   std::lock_guard<std::mutex> lk(s.mu);
-  for (auto& ev : s.pending) {
-    TT_CUDA(cudaEventSynchronize(ev.second));
-    float ms = 0.f;
-    TT_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
-    s.seconds += ms * 1e-3;
-    s.pool.push_back(ev);
-  }
-  s.pending.clear();
+  resolve(s);
   if (flops) *flops = s.flops;
   if (seconds) *seconds = s.seconds;
+  if (calls) *calls = s.calls;
 }
 
 void stats_reset() {
-  double f, t;
-  stats_read(&f, &t);
-  Stats& s = stats();
-  std::lock_guard<std::mutex> lk(s.mu);
-  s.flops = 0.0;
-  s.seconds = 0.0;
+  for (int key = 0; key < 2; ++key) {
+    Stats& s = stats(key);
+    std::lock_guard<std::mutex> lk(s.mu);
+    resolve(s);
+    s.flops = 0.0;
+    s.seconds = 0.0;
+    s.calls = 0;
+  }
 }
 
 }  // namespace ttsdp

@@ -30,9 +30,10 @@ void to_f32(const double* a, float* b, size_t n, cudaStream_t st);
 void to_f64(const float* a, double* b, size_t n, cudaStream_t st);
 
 // Contraction statistics (device time via CUDA events and algorithmic flops).
-void stats_begin(cudaStream_t st);
-void stats_end(cudaStream_t st, double flops);
-void stats_read(double* flops, double* seconds);
+// key 0: whole contraction calls; key 1: tensor-core GEMM launches.
+void stats_begin(cudaStream_t st, int key = 0);
+void stats_end(cudaStream_t st, double flops, int key = 0);
+void stats_read(double* flops, double* seconds, int key = 0, unsigned long long* calls = nullptr);
 void stats_reset();
 
 }  // namespace ttsdp

@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
     Vc[idx] = i == j ? T(1) : T(0);
   }
   __syncthreads();
-  const T tol = T(8) * eps_of<T>();
+  // rotation threshold: a length-m dot product carries about sqrt(m) eps of
+  // rounding noise, so a smaller threshold never lets the sweeps terminate
+  const T tol = T(4) * sqrt(T(m)) * eps_of<T>();
   // columns whose squared norm is below (eps ||A||_F)^2 are numerical noise:
   // rotating against them cannot change any singular value above that level
   // and would keep the sweep from terminating on rank-deficient inputs

@@ -15,6 +15,7 @@
 #include "gemm.cuh"
 #include "linalg.cuh"
 #include "solver.cuh"
+#include "tc_gemm.cuh"
 
 namespace ttsdp {
 
@@ -464,11 +465,15 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         int nk = keep + std::max(extra, 0);
         DBuf<double> u((size_t)rows * nk);
         dev_copy2d(u.get(), nk, U.get(), kk, rows, keep, 1.0, st);
-        if (extra > 0) {
-          std::vector<double> rndv = rnd.draw((size_t)rows * extra);
-          DBuf<double> rr_((size_t)rows * extra);
-          upload(rr_.get(), rndv);
-          dev_copy2d(u.get() + keep, nk, rr_.get(), extra, rows, extra, 1.0, st);
+        // with a kick, or when the SVD ran in FP32, the new frame core is
+        // re-orthonormalised in FP64 (the SVD only chooses the subspace)
+        if (extra > 0 || prec != TT_FP64) {
+          if (extra > 0) {
+            std::vector<double> rndv = rnd.draw((size_t)rows * extra);
+            DBuf<double> rr_((size_t)rows * extra);
+            upload(rr_.get(), rndv);
+            dev_copy2d(u.get() + keep, nk, rr_.get(), extra, rows, extra, 1.0, st);
+          }
           DBuf<double> Q((size_t)rows * nk), Rq((size_t)nk * nk);
           qr_thin<double>(MatView<double>{u.get(), rows, nk, nk, 1}, Q.get(), Rq.get(), st);
           dev_copy(u.get(), Q.get(), (size_t)rows * nk, st);
@@ -508,11 +513,13 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         DBuf<double> vk((size_t)cols * keep);
         transpose<double>(keep, cols, vt_keep.get(), vk.get(), st);
         dev_copy2d(v.get(), nk, vk.get(), keep, cols, keep, 1.0, st);
-        if (extra > 0) {
-          std::vector<double> rndv = rnd.draw((size_t)cols * extra);
-          DBuf<double> rr_((size_t)cols * extra);
-          upload(rr_.get(), rndv);
-          dev_copy2d(v.get() + keep, nk, rr_.get(), extra, cols, extra, 1.0, st);
+        if (extra > 0 || prec != TT_FP64) {
+          if (extra > 0) {
+            std::vector<double> rndv = rnd.draw((size_t)cols * extra);
+            DBuf<double> rr_((size_t)cols * extra);
+            upload(rr_.get(), rndv);
+            dev_copy2d(v.get() + keep, nk, rr_.get(), extra, cols, extra, 1.0, st);
+          }
           DBuf<double> Q((size_t)cols * nk), Rq((size_t)nk * nk);
           qr_thin<double>(MatView<double>{v.get(), cols, nk, nk, 1}, Q.get(), Rq.get(), st);
           dev_copy(v.get(), Q.get(), (size_t)cols * nk, st);
@@ -1055,6 +1062,8 @@ IterLog Solver::iterate() {
   log.max_rank_X = X_.maxrank();
   log.max_rank_Z = Z_.maxrank();
   log.gmres_iters = gmres_iters_;
+  if ((o_.prec == TT_MIXED_TF32 || o_.prec == TT_MIXED_BF16) && tc_check_error(true))
+    throw TTError(TT_E_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
   TT_CUDA(cudaEventRecord(e1, st));
   TT_CUDA(cudaEventSynchronize(e1));
   float msec = 0.f;

@@ -21,6 +21,7 @@
 
 #include <mutex>
 
+#include "contract.cuh"
 #include "tc_gemm.cuh"
 
 namespace ttsdp {
@@ -362,8 +363,10 @@ bool tc_stage2(int prec, long long rw, long long R, long long R2, long long m, l
     count_launch();
     count_launch();
     check_launch("tc pack");
-    // C layout [(i,q)][(a',b)], fp32
+    // C layout [(i,q)][(a',b)], fp32; timed as one kernel with its algorithmic K
+    stats_begin(st, 1);
     tc_gemm_tn(prec, (int)M, (int)N, (int)Kp, 1, a.get(), 0, b.get(), 0, t2, 0, st);
+    stats_end(st, 2.0 * (double)M * (double)N * (double)Kr, 1);
     return true;
   }
 }
