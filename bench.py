@@ -120,6 +120,21 @@ def _dist():
     return rank, world, local
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Replicas: each rank solves its own instance, drawn from seed + rank."""
+    return seed + rank
+
+
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 def run_reference(a):
     """The oracle on the host cores: dense primal-dual IPM (O2) to the target gap on the same instance."""
     rank, world, _ = _dist()
@@ -176,7 +191,7 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = WORKLOADS[a.workload]
-    seed = a.seed + rank  # replicas: one independent instance per rank
+    seed = replica_seed(a.seed, rank)
     inst = _instance(w, seed)
     stream = torch.cuda.current_stream()
     # row a1 (setup, untimed): graph -> TT on the device
@@ -218,10 +233,7 @@ def run_ours(a):
     reached = bool(conv)
     ttg = sum(i["seconds"] for i in infos if not i["converged"]) if reached else total
     last = conv[0] if reached else infos[-1]
-    if world > 1:
-        t = torch.tensor([ttg, total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ttg, total = float(t[0]), float(t[1])
+    ttg, total = max_over_ranks([ttg, total], device="cuda")
     # end to end through the C ABI with host buffers: H2D of the weight cores,
     # the solve, D2H of the primal iterate X
     e2e = None

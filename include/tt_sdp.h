@@ -224,6 +224,8 @@ typedef struct {
   int32_t direction;   /* 0 XZ, 1 AHO                                                 */
   double seconds;      /* device time of the iteration (CUDA events)                 */
   int64_t gmres_iters; /* local GMRES operator products so far                       */
+  int64_t pred_used;      /* bonds rounded by the predicted-rank range finder so far   */
+  int64_t pred_fallbacks; /* predicted bonds that fell back to the adaptive SVD        */
 } tt_sdp_iter_info;
 
 typedef struct {
@@ -271,6 +273,44 @@ tt_status tt_sdp_get_iterate(tt_sdp_ctx* ctx, int32_t which, int32_t* ranks, dou
 int32_t tt_sdp_order(const tt_sdp_ctx* ctx);
 
 void tt_sdp_destroy(tt_sdp_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Learned per-bond rank predictor (row a9, learned variant). The paper picks
+ * every rank by the adaptive SVD; this library adds a small network that
+ * predicts the rank the adaptive SVD would choose, so that a rounding can use
+ * a fixed-rank randomised range finder (Halko, Martinsson and Tropp) whose
+ * sketch product runs on the TF32 tensor cores. The exact FP64 truncation
+ * error of the sketched bond is checked against the bond tolerance; when it
+ * exceeds it (or the rank cap would bind) the bond falls back to the
+ * adaptive SVD, which stays the judge. Network: 9 features -> 64 -> 64 -> 64
+ * -> 1, tanh hidden layers, sigmoid output = rank / cap, trained on the GPU
+ * (mean squared error, Adam) by the library's own kernels. Features of a
+ * bond: one-hot variable (X, Y, T, Z), bond position k/(d-2), log10(mu)/10,
+ * input rank / cap, previous rank of that bond / cap, iteration / max_iters.
+ * All arrays below are HOST arrays.
+ * ------------------------------------------------------------------------- */
+typedef struct tt_rankpred tt_rankpred;
+
+/* Number of float parameters (9089). */
+int32_t tt_rankpred_param_count(void);
+/* Xavier-initialised network from the SplitMix64 stream `seed`. */
+tt_status tt_rankpred_create(uint64_t seed, tt_rankpred** out);
+void tt_rankpred_destroy(tt_rankpred* p);
+tt_status tt_rankpred_get_params(const tt_rankpred* p, float* out);
+tt_status tt_rankpred_set_params(tt_rankpred* p, const float* in);
+/* Mean squared error on (X: n x 9, t: n) and its gradient (param_count floats). */
+tt_status tt_rankpred_grad(tt_rankpred* p, const float* X, const float* t, int32_t n, float* grad, float* loss);
+/* Adam (beta 0.9 / 0.999) on shuffled mini-batches; *loss = final full-data loss. */
+tt_status tt_rankpred_train(tt_rankpred* p, const float* X, const float* t, int32_t n, int32_t epochs,
+                            int32_t batch, float lr, uint64_t seed, float* loss);
+/* y (n values in (0, 1)) for the feature rows X (n x 9). */
+tt_status tt_rankpred_predict(const tt_rankpred* p, const float* X, int32_t n, float* y);
+/* Attach a copy of the predictor to a context (NULL detaches). */
+tt_status tt_sdp_set_rank_predictor(tt_sdp_ctx* ctx, const tt_rankpred* p);
+/* Record (features, adaptive-SVD rank / cap) of every bond rounded by the adaptive SVD. */
+tt_status tt_sdp_set_trace(tt_sdp_ctx* ctx, int32_t on);
+/* Copy the recorded trace: X (n x 9 floats) and t (n floats); with X == NULL only *n is set. */
+tt_status tt_sdp_get_trace(tt_sdp_ctx* ctx, float* X, float* t, size_t* n);
 
 /* ---------------------------------------------------------------------------
  * Diagnostics

@@ -280,6 +280,22 @@ class Context:
             off += size
         return out
 
+    def set_rank_predictor(self, pred):
+        _check(lib().tt_sdp_set_rank_predictor(self._h, pred._h if pred is not None else None),
+               "tt_sdp_set_rank_predictor")
+
+    def set_trace(self, on=True):
+        _check(lib().tt_sdp_set_trace(self._h, 1 if on else 0), "tt_sdp_set_trace")
+
+    def trace(self):
+        n = ctypes.c_size_t(0)
+        _check(lib().tt_sdp_get_trace(self._h, None, None, ctypes.byref(n)), "tt_sdp_get_trace")
+        X = np.empty((n.value, 9), dtype=np.float32)
+        t = np.empty(n.value, dtype=np.float32)
+        if n.value:
+            _check(lib().tt_sdp_get_trace(self._h, X.ctypes.data, t.ctypes.data, ctypes.byref(n)), "tt_sdp_get_trace")
+        return X, t
+
     def close(self):
         if self._h:
             lib().tt_sdp_destroy(self._h)
@@ -288,6 +304,56 @@ class Context:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class RankPredictor:
+    """The learned per-bond rank predictor (tt_rankpred); arrays are host numpy float32."""
+
+    def __init__(self, seed: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(lib().tt_rankpred_create(seed, ctypes.byref(self._h)), "tt_rankpred_create")
+        self.nparam = int(lib().tt_rankpred_param_count())
+
+    @staticmethod
+    def _f32(a):
+        return np.ascontiguousarray(a, dtype=np.float32)
+
+    def params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(lib().tt_rankpred_get_params(self._h, out.ctypes.data), "tt_rankpred_get_params")
+        return out
+
+    def set_params(self, p):
+        p = self._f32(p)
+        _check(lib().tt_rankpred_set_params(self._h, p.ctypes.data), "tt_rankpred_set_params")
+
+    def grad(self, X, t):
+        X, t = self._f32(X), self._f32(t)
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(lib().tt_rankpred_grad(self._h, X.ctypes.data, t.ctypes.data, len(t), g.ctypes.data,
+                                      ctypes.byref(loss)), "tt_rankpred_grad")
+        return loss.value, g
+
+    def train(self, X, t, epochs=200, batch=256, lr=1e-3, seed=0):
+        X, t = self._f32(X), self._f32(t)
+        loss = ctypes.c_float(0.0)
+        _check(lib().tt_rankpred_train(self._h, X.ctypes.data, t.ctypes.data, len(t), epochs, batch, lr, seed,
+                                       ctypes.byref(loss)), "tt_rankpred_train")
+        return loss.value
+
+    def predict(self, X):
+        X = self._f32(X)
+        y = np.empty(X.shape[0], dtype=np.float32)
+        _check(lib().tt_rankpred_predict(self._h, X.ctypes.data, X.shape[0], y.ctypes.data), "tt_rankpred_predict")
+        return y
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().tt_rankpred_destroy(self._h)
         except Exception:
             pass
 

@@ -43,7 +43,7 @@ class IterInfo(ctypes.Structure):
                 ("rel_d", c_double), ("rel_gap", c_double), ("pobj", c_double), ("dobj", c_double),
                 ("alpha_p", c_double), ("alpha_d", c_double), ("max_rank_X", c_int32), ("max_rank_Z", c_int32),
                 ("max_rank_W", c_int32), ("sweeps", c_int32), ("direction", c_int32), ("seconds", c_double),
-                ("gmres_iters", ctypes.c_int64)]
+                ("gmres_iters", ctypes.c_int64), ("pred_used", ctypes.c_int64), ("pred_fallbacks", ctypes.c_int64)]
 
 
 class Result(ctypes.Structure):
@@ -90,6 +90,18 @@ SIGNATURES = {
     "tt_contraction_stats": (None, [P_double, P_double]),
     "tt_contraction_stats_reset": (None, []),
     "tt_profile_report": (c_size_t, [ctypes.c_char_p, c_size_t]),
+    "tt_rankpred_param_count": (c_int32, []),
+    "tt_rankpred_create": (c_int32, [ctypes.c_uint64, ctypes.POINTER(c_void_p)]),
+    "tt_rankpred_destroy": (None, [c_void_p]),
+    "tt_rankpred_get_params": (c_int32, [c_void_p, c_void_p]),
+    "tt_rankpred_set_params": (c_int32, [c_void_p, c_void_p]),
+    "tt_rankpred_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "tt_rankpred_train": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, ctypes.c_float,
+                                    ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]),
+    "tt_rankpred_predict": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "tt_sdp_set_rank_predictor": (c_int32, [c_void_p, c_void_p]),
+    "tt_sdp_set_trace": (c_int32, [c_void_p, c_int32]),
+    "tt_sdp_get_trace": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_size_t)]),
     "tt_tc_stats": (None, [P_double, P_double, ctypes.POINTER(ctypes.c_uint64)]),
 }
 

@@ -385,6 +385,8 @@ tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info) {
     info->direction = l.direction;
     info->seconds = l.seconds;
     info->gmres_iters = l.gmres_iters;
+    info->pred_used = l.pred_used;
+    info->pred_fallbacks = l.pred_fallbacks;
   });
 }
 
@@ -459,3 +461,106 @@ extern "C" size_t tt_profile_report(char* buf, size_t cap) {
   }
   return s.size();
 }
+
+// ---------------------------------------------------------------------------
+// learned rank predictor
+// ---------------------------------------------------------------------------
+#include "rankpred.cuh"
+
+struct tt_rankpred {
+  std::shared_ptr<RankPredictor> p;
+};
+
+extern "C" {
+
+int32_t tt_rankpred_param_count(void) { return kPredParams; }
+
+tt_status tt_rankpred_create(uint64_t seed, tt_rankpred** out) {
+  return guarded(nullptr, [&] {
+    TT_CHECK(out, TT_E_INVALID_ARG, "null output");
+    auto* r = new tt_rankpred;
+    try {
+      r->p = std::make_shared<RankPredictor>(seed);
+    } catch (...) {
+      delete r;
+      throw;
+    }
+    *out = r;
+  });
+}
+
+void tt_rankpred_destroy(tt_rankpred* p) { delete p; }
+
+tt_status tt_rankpred_get_params(const tt_rankpred* p, float* out) {
+  return guarded(nullptr, [&] {
+    TT_CHECK(p && out, TT_E_INVALID_ARG, "null argument");
+    p->p->get_params(out);
+  });
+}
+
+tt_status tt_rankpred_set_params(tt_rankpred* p, const float* in) {
+  return guarded(nullptr, [&] {
+    TT_CHECK(p && in, TT_E_INVALID_ARG, "null argument");
+    p->p->set_params(in);
+  });
+}
+
+tt_status tt_rankpred_grad(tt_rankpred* p, const float* X, const float* t, int32_t n, float* grad, float* loss) {
+  return guarded(nullptr, [&] {
+    TT_CHECK(p && X && t && grad && loss && n > 0, TT_E_INVALID_ARG, "bad arguments");
+    *loss = p->p->grad(X, t, n, grad);
+  });
+}
+
+tt_status tt_rankpred_train(tt_rankpred* p, const float* X, const float* t, int32_t n, int32_t epochs, int32_t batch,
+                            float lr, uint64_t seed, float* loss) {
+  return guarded(nullptr, [&] {
+    TT_CHECK(p && X && t && loss && n > 0 && epochs > 0 && batch > 0 && lr > 0, TT_E_INVALID_ARG, "bad arguments");
+    *loss = p->p->train(X, t, n, epochs, batch, lr, seed);
+  });
+}
+
+tt_status tt_rankpred_predict(const tt_rankpred* p, const float* X, int32_t n, float* y) {
+  return guarded(nullptr, [&] {
+    TT_CHECK(p && X && y && n > 0, TT_E_INVALID_ARG, "bad arguments");
+    std::vector<float> xs(X, X + (size_t)n * kPredIn);
+    std::vector<float> r = p->p->predict(xs, n);
+    std::copy(r.begin(), r.end(), y);
+  });
+}
+
+tt_status tt_sdp_set_rank_predictor(tt_sdp_ctx* ctx, const tt_rankpred* p) {
+  if (!ctx) return TT_E_INVALID_ARG;
+  return guarded(ctx->stream, [&] {
+    if (!p) {
+      ctx->solver->set_predictor(nullptr);
+      return;
+    }
+    std::vector<float> params(kPredParams);
+    p->p->get_params(params.data());
+    auto copy = std::make_shared<RankPredictor>(0);
+    copy->set_params(params.data());
+    ctx->solver->set_predictor(copy);
+  });
+}
+
+tt_status tt_sdp_set_trace(tt_sdp_ctx* ctx, int32_t on) {
+  if (!ctx) return TT_E_INVALID_ARG;
+  ctx->solver->set_trace(on != 0);
+  return TT_OK;
+}
+
+tt_status tt_sdp_get_trace(tt_sdp_ctx* ctx, float* X, float* t, size_t* n) {
+  if (!ctx || !n) return TT_E_INVALID_ARG;
+  const auto& tx = ctx->solver->trace_x();
+  const auto& ty = ctx->solver->trace_y();
+  if (X) {
+    if (*n < ty.size() || !t) return TT_E_NOMEM;
+    std::copy(tx.begin(), tx.end(), X);
+    std::copy(ty.begin(), ty.end(), t);
+  }
+  *n = ty.size();
+  return TT_OK;
+}
+
+}  // extern "C"

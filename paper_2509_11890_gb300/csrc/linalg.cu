@@ -157,7 +157,10 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
     T loc = T(0);
     for (long long idx = tid; idx < (long long)m * n; idx += kThreads) loc += Wc[idx] * Wc[idx];
     T fro2 = block_sum(loc, red);
-    if (tid == 0) s_floor = eps_of<T>() * eps_of<T>() * fro2;
+    // rotating a large column against a tiny one leaves rounding noise of
+    // size ~eps |large| in the tiny one, so the floor sits at the noise level
+    // of the whole matrix, (sqrt(m) eps ||A||_F)^2
+    if (tid == 0) s_floor = T(m) * eps_of<T>() * eps_of<T>() * fro2;
     __syncthreads();
   }
   const T floor2 = s_floor;

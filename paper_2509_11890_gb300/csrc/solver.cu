@@ -980,9 +980,24 @@ void Solver::steps(const DTT& dX, const DTT& dT, const DTT& dZ, double* ap, doub
   *ad = std::min(1.0, o_.damping * a_d);
 }
 
-DTT Solver::round_psd(const DTT& Mx, double delta, const DTT* shift) {
+DTT Solver::round_psd(const DTT& Mx, double delta, const DTT* shift, int var_id) {
   double sn = shift ? tt_norm(vecv(*shift)) : 0.0;
-  auto rz = tt_round(vecv(Mx), delta / (1.0 + sn), o_.rank_cap);
+  std::vector<int>& prev = prev_[var_id & 3];
+  if ((int)prev.size() != p_.d + 1) prev.assign(p_.d + 1, 0);
+  RoundHook hook;
+  hook.var_id = var_id;
+  hook.mu = mu_now_;
+  hook.iter_frac = (double)it_ / (double)std::max(o_.max_iters, 1);
+  hook.prev = &prev;
+  hook.pred = pred_.get();
+  hook.rnd = &rnd_;
+  if (trace_) {
+    hook.trace_x = &trace_x_;
+    hook.trace_y = &trace_y_;
+  }
+  auto rz = tt_round(vecv(Mx), delta / (1.0 + sn), o_.rank_cap, &hook);
+  pred_used_ += hook.used;
+  pred_fallbacks_ += hook.fallbacks;
   DTT rounded = unvec(rz.first);
   double zeta = rz.second;
   if (shift && zeta > 0) rounded = tt_add(rounded, *shift, 1.0, zeta);
@@ -1004,6 +1019,7 @@ IterLog Solver::iterate() {
     ms = measures();
   }
   log.mu = ms.mu;
+  mu_now_ = ms.mu;
   log.rel_p = ms.rel_p;
   log.rel_d = ms.rel_d;
   log.rel_gap = ms.rel_gap;
@@ -1053,15 +1069,17 @@ IterLog Solver::iterate() {
     log.max_rank_W = w_->frame.maxrank();
     const double tol_p = eta_ * (1.0 + nB_) / 10.0, tol_d = eta_ * (1.0 + nC_) / 10.0;
     ProfScope ps_round("ipm.round");
-    X_ = round_psd(tt_add(X_, dX, 1.0, ap), tol_p, &I_);
-    Z_ = round_psd(tt_add(Z_, dZ, 1.0, ad), tol_d, &I_);
-    Y_ = round_psd(tt_add(Y_, dY, 1.0, ad), tol_d, nullptr);
-    if (p_.ineq) T_ = round_psd(tt_add(T_, dT, 1.0, ad), tol_d, &p_.ones_t);
+    X_ = round_psd(tt_add(X_, dX, 1.0, ap), tol_p, &I_, 0);
+    Z_ = round_psd(tt_add(Z_, dZ, 1.0, ad), tol_d, &I_, 3);
+    Y_ = round_psd(tt_add(Y_, dY, 1.0, ad), tol_d, nullptr, 1);
+    if (p_.ineq) T_ = round_psd(tt_add(T_, dT, 1.0, ad), tol_d, &p_.ones_t, 2);
     ++it_;
   }
   log.max_rank_X = X_.maxrank();
   log.max_rank_Z = Z_.maxrank();
   log.gmres_iters = gmres_iters_;
+  log.pred_used = pred_used_;
+  log.pred_fallbacks = pred_fallbacks_;
   if ((o_.prec == TT_MIXED_TF32 || o_.prec == TT_MIXED_BF16) && tc_check_error(true))
     throw TTError(TT_E_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
   TT_CUDA(cudaEventRecord(e1, st));

@@ -49,7 +49,10 @@ struct IterLog {
   int max_rank_X = 0, max_rank_Z = 0, max_rank_W = 0;
   double seconds = 0;
   long long gmres_iters = 0;
+  long long pred_used = 0, pred_fallbacks = 0;
 };
+
+class RankPredictor;
 
 class Solver {
  public:
@@ -63,6 +66,12 @@ class Solver {
   int order() const { return p_.d; }
   int iter() const { return it_; }
   const Options& options() const { return o_; }
+  // learned rank predictor for the roundings (null: adaptive SVD only)
+  void set_predictor(std::shared_ptr<RankPredictor> p) { pred_ = std::move(p); }
+  // record (features, adaptive-SVD rank / cap) of every rounded bond
+  void set_trace(bool on) { trace_ = on; }
+  const std::vector<float>& trace_x() const { return trace_x_; }
+  const std::vector<float>& trace_y() const { return trace_y_; }
 
  private:
   struct Measures {
@@ -75,7 +84,7 @@ class Solver {
   void steps(const DTT& dX, const DTT& dT, const DTT& dZ, double* ap, double* ad);
   double max_step(const DTT& M, const DTT& dM, DTT* e);
   double max_step_diag(const DTT& v, const DTT& dv, DTT* e);
-  DTT round_psd(const DTT& M, double delta, const DTT* shift);
+  DTT round_psd(const DTT& M, double delta, const DTT* shift, int var_id);
 
   Problem p_;
   Options o_;
@@ -84,6 +93,12 @@ class Solver {
   double eta_, nB_, nC_;
   int it_ = 0, N_;
   long long gmres_iters_ = 0;
+  double mu_now_ = 1.0;
+  std::shared_ptr<RankPredictor> pred_;
+  bool trace_ = false;
+  std::vector<float> trace_x_, trace_y_;
+  std::vector<int> prev_[4];
+  long long pred_used_ = 0, pred_fallbacks_ = 0;
   std::unique_ptr<BlockTT> w_;
   DTT eX_, eZ_, eT_, eS_;
   bool haveX_ = false, haveZ_ = false, haveT_ = false, haveS_ = false;

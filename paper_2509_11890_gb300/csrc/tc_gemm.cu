@@ -328,6 +328,36 @@ void tc_gemm_tn(int prec, int M, int N, int K, int batch, const void* A, long lo
   }
 }
 
+namespace {
+// dst (rows x ld, fp32, zero-padded columns) <- src (rows x cols, fp64, row stride sld)
+__global__ void pack_f64_kernel(const double* __restrict__ src, int rows, int cols, long long sld, long long ld,
+                                float* dst) {
+  const long long tot = (long long)rows * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / ld, j = e % ld;
+    dst[e] = j < cols ? (float)src[i * sld + j] : 0.f;
+  }
+}
+__global__ void widen_kernel(const float* __restrict__ src, long long n, double* dst) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+}  // namespace
+
+void tc_gemm_f64_tn(int M, int N, int K, const double* A, long long lda, const double* B, long long ldb, double* C,
+                    cudaStream_t st) {
+  const long long Kp = (K + 7) / 8 * 8;
+  DBuf<float> a((size_t)M * Kp), b((size_t)N * Kp), c((size_t)M * N);
+  pack_f64_kernel<<<grid1((long long)M * Kp), 256, 0, st>>>(A, M, K, lda, Kp, a.get());
+  pack_f64_kernel<<<grid1((long long)N * Kp), 256, 0, st>>>(B, N, K, ldb, Kp, b.get());
+  count_launch();
+  count_launch();
+  tc_gemm_tn(TT_MIXED_TF32, M, N, (int)Kp, 1, a.get(), 0, b.get(), 0, c.get(), 0, st);
+  widen_kernel<<<grid1((long long)M * N), 256, 0, st>>>(c.get(), (long long)M * N, C);
+  count_launch();
+  check_launch("tc_gemm_f64_tn");
+}
+
 int tc_check_error(bool reset) {
   int h = 0;
   TT_CUDA(cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int)));

@@ -21,6 +21,12 @@ bool tc_stage2(int prec, long long rw, long long R, long long R2, long long m, l
 void tc_gemm_tn(int prec, int M, int N, int K, int batch, const void* A, long long sA,
                 const void* B, long long sB, float* C, long long sC, cudaStream_t st);
 
+// C (M x N, fp64) = A (M x K, fp64, row stride lda) B (N x K, fp64, row stride
+// ldb)^T with the product on the TF32 tensor cores (operands rounded to TF32,
+// FP32 accumulation). Used by the randomised range finder of TT rounding.
+void tc_gemm_f64_tn(int M, int N, int K, const double* A, long long lda, const double* B, long long ldb, double* C,
+                    cudaStream_t st);
+
 // Reads (and with reset clears) the error word a tensor-core kernel sets when
 // one of its bounded waits gives up; 0 means no failure.
 int tc_check_error(bool reset);

@@ -6,6 +6,8 @@
 
 #include "gemm.cuh"
 #include "linalg.cuh"
+#include "rankpred.cuh"
+#include "tc_gemm.cuh"
 #include "tt.cuh"
 
 namespace ttsdp {
@@ -552,16 +554,106 @@ int truncation_rank(const std::vector<double>& s, double thr, int cap) {
   return keep;
 }
 
-std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap) {
+// Features of the learned rank predictor for bond k (9 values): one-hot variable,
+// bond position, log10(mu) / 10, input rank / cap, previous rank / cap, iteration fraction.
+static void bond_features(const RoundHook& h, int k, int d, int in_rank, int cap, float* f) {
+  for (int i = 0; i < 4; ++i) f[i] = (h.var_id == i) ? 1.f : 0.f;
+  f[4] = d > 2 ? (float)k / (float)(d - 2) : 0.f;
+  f[5] = (float)(std::log10(std::max(h.mu, 1e-300)) / 10.0);
+  f[6] = (float)in_rank / (float)std::max(cap, 1);
+  const int prev = h.prev && (int)h.prev->size() > k + 1 ? (*h.prev)[k + 1] : 0;
+  f[7] = (float)prev / (float)std::max(cap, 1);
+  f[8] = (float)h.iter_frac;
+}
+
+// One bond by the fixed-rank randomised range finder (Halko, Martinsson & Tropp
+// 2011): Y = A Omega on the TF32 tensor cores, Q = qr(Y), B = Q^T A and the SVD
+// of the small B in FP64. The exact FP64 truncation error ||A||^2 - sum of the
+// kept sigma^2 must stay within the bond threshold, otherwise the caller falls
+// back to the adaptive SVD. Returns the kept rank (0: rejected).
+static int round_bond_sketch(DTT& t, int k, int l, double thr, int cap, Counter& rnd, double* err2) {
+  cudaStream_t st = cur_stream();
+  const int M = t.m * t.n, r = t.r[k], r2 = t.r[k + 1], rows = r * M;
+  const double* A = t.core(k);
+  DBuf<double> Om((size_t)l * r2), Y((size_t)rows * l), Q((size_t)rows * l), Rq((size_t)l * l), Bm((size_t)l * r2);
+  {
+    std::vector<double> h = rnd.draw((size_t)l * r2);
+    TT_CUDA(cudaMemcpyAsync(Om.get(), h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    TT_CUDA(cudaStreamSynchronize(st));
+  }
+  tc_gemm_f64_tn(rows, l, r2, A, r2, Om.get(), r2, Y.get(), st);  // Y = A Omega, Omega^T stored l x r2
+  qr_thin<double>(MatView<double>{Y.get(), rows, l, l, 1}, Q.get(), Rq.get(), st);
+  gemm_rm<double>(true, false, l, r2, rows, 1.0, Q.get(), l, 0, A, r2, 0, 0.0, Bm.get(), r2, 0, 1, st);
+  const int kk = std::min(l, r2);
+  DBuf<double> UB((size_t)l * kk), S(kk), Vt((size_t)kk * r2);
+  svd_thin<double>(MatView<double>{Bm.get(), l, r2, r2, 1}, UB.get(), S.get(), Vt.get(), st);
+  std::vector<double> hs(kk);
+  TT_CUDA(cudaMemcpyAsync(hs.data(), S.get(), kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+  const double a2 = dev_dot(A, A, (size_t)rows * r2, st);
+  double s2 = 0.0;
+  for (double v : hs) s2 += v * v;
+  const double missing = std::max(a2 - s2, 0.0);
+  // smallest rank whose error (missing energy + discarded sigma^2) is within thr^2
+  double tail = missing;
+  int keep = kk;
+  if (tail > thr * thr) return 0;
+  for (int j = kk - 1; j >= 1; --j) {
+    if (tail + hs[j] * hs[j] <= thr * thr) {
+      tail += hs[j] * hs[j];
+      keep = j;
+    } else {
+      break;
+    }
+  }
+  if (cap > 0 && keep > cap) return 0;  // the cap would bind: let the adaptive SVD decide
+  // new core = Q UB[:, :keep]; next core = diag(S) Vt[:keep] core_{k+1}
+  auto nc = std::make_shared<DBuf<double>>((size_t)rows * keep);
+  gemm_rm<double>(false, false, rows, keep, l, 1.0, Q.get(), l, 0, UB.get(), kk, 0, 0.0, nc->get(), keep, 0, 1, st);
+  dev_scale_rows(Vt.get(), keep, r2, S.get(), st);
+  const int r3 = t.r[k + 2];
+  auto xc = std::make_shared<DBuf<double>>((size_t)keep * M * r3);
+  gemm_rm<double>(false, false, keep, M * r3, r2, 1.0, Vt.get(), r2, 0, t.core(k + 1), M * r3, 0, 0.0, xc->get(),
+                  M * r3, 0, 1, st);
+  t.c[k] = nc;
+  t.c[k + 1] = xc;
+  t.r[k + 1] = keep;
+  *err2 = tail;
+  return keep;
+}
+
+std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* hook) {
   const int d = a.d, M = a.m * a.n;
   cudaStream_t st = cur_stream();
   DTT t = tt_orth_right(a);
   const double thr = delta / std::sqrt((double)(d > 1 ? d - 1 : 1));
   double zeta2 = 0.0;
+  // features and predicted ranks of all bonds (one MLP evaluation)
+  std::vector<float> feats;
+  std::vector<float> pred;
+  if (hook && d > 1 && (hook->pred || hook->trace_x)) {
+    feats.resize((size_t)(d - 1) * kPredIn);
+    for (int k = 0; k + 1 < d; ++k) bond_features(*hook, k, d, t.r[k + 1], cap, &feats[(size_t)k * kPredIn]);
+    if (hook->pred) pred = hook->pred->predict(feats, d - 1);
+  }
   for (int k = 0; k + 1 < d; ++k) {
     int r = t.r[k], r2 = t.r[k + 1];
     int rows = r * M;
     int kk = rows < r2 ? rows : r2;
+    if (!pred.empty() && hook->rnd) {
+      const int rh = std::max(1, (int)std::ceil(pred[k] * std::max(cap, 1)));
+      const int l = std::min(rh + 4, kk);
+      if (l < kk) {
+        double e2 = 0.0;
+        const int kept = round_bond_sketch(t, k, l, thr, cap, *hook->rnd, &e2);
+        if (kept > 0) {
+          zeta2 += e2;
+          ++hook->used;
+          if (hook->prev && (int)hook->prev->size() > k + 1) (*hook->prev)[k + 1] = kept;
+          continue;
+        }
+        ++hook->fallbacks;
+      }
+    }
     DBuf<double> U((size_t)rows * kk), S((size_t)kk), Vt((size_t)kk * r2);
     MatView<double> v{t.core(k), rows, r2, r2, 1};
     svd_thin<double>(v, U.get(), S.get(), Vt.get(), st);
@@ -570,6 +662,12 @@ std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap) {
     TT_CUDA(cudaStreamSynchronize(st));
     int keep = truncation_rank(hs, thr, cap);
     for (int j = keep; j < kk; ++j) zeta2 += hs[j] * hs[j];
+    if (hook && hook->trace_x && !feats.empty()) {  // the adaptive SVD's choice is the label
+      hook->trace_x->insert(hook->trace_x->end(), feats.begin() + (size_t)k * kPredIn,
+                            feats.begin() + (size_t)(k + 1) * kPredIn);
+      hook->trace_y->push_back((float)keep / (float)std::max(cap, 1));
+    }
+    if (hook && hook->prev && (int)hook->prev->size() > k + 1) (*hook->prev)[k + 1] = keep;
     auto nc = std::make_shared<DBuf<double>>((size_t)rows * keep);
     dev_copy2d(nc->get(), keep, U.get(), kk, rows, keep, 1.0, st);
     // next core <- diag(S[:keep]) Vt[:keep] core_{k+1}

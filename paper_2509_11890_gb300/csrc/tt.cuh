@@ -62,7 +62,23 @@ double tt_norm(const DTT& a);
 // the smallest rank whose discarded energy is <= (delta / sqrt(d-1))^2, then
 // at most cap (cap <= 0: none). Works on the vector view (m * n per core).
 // Returns the rounded TT (same m, n) and zeta = sqrt(sum discarded sigma^2).
-std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap);
+class RankPredictor;
+struct Counter;
+
+// Optional context of one rounding: features of the learned rank predictor,
+// the predictor itself, trace collection and counters.
+struct RoundHook {
+  int var_id = 0;                      // 0 X, 1 Y, 2 T, 3 Z
+  double mu = 1.0, iter_frac = 0.0;
+  std::vector<int>* prev = nullptr;    // previous rounded ranks of this variable (d + 1), updated
+  const RankPredictor* pred = nullptr; // when set: fixed-rank randomised range finder per bond
+  std::vector<float>* trace_x = nullptr;
+  std::vector<float>* trace_y = nullptr;
+  Counter* rnd = nullptr;              // sketch matrices
+  long long used = 0, fallbacks = 0;
+};
+
+std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* hook = nullptr);
 
 // TT-SVD (Oseledets 2011) of a dense n^d x n^d matrix given row-major on the
 // device: the matrix is permuted to its vec_TT order (Section 3.1) and split
