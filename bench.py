@@ -33,6 +33,8 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "maxcut_d10_kron_er_cap64": dict(kind="maxcut_er", d=10, cap=64),
     "maxcut_d6_kron_cap16": dict(kind="maxcut", d=6, cap=16),
+    # 64 independent Kronecker Max-Cut instances, d ~ U{6..11}, unit weights
+    "maxcut_batch64_d6to11_cap64": dict(kind="batch", count=64, d_lo=6, d_hi=11, cap=64, d=11),
 }
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}
@@ -48,6 +50,9 @@ def _args():
     p.add_argument("--precision", default="tf32", choices=sorted(PREC))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workers", type=int, default=16, help="host threads of the batched solve")
+    p.add_argument("--sequential", type=int, default=8,
+                   help="batched workload: instances also solved one at a time in FP64 (0: none)")
     return p.parse_args()
 
 
@@ -142,6 +147,8 @@ def run_reference(a):
         return 0
     from oracle import sdp_dense as sd
     w = WORKLOADS[a.workload]
+    if w["kind"] == "batch":
+        return _run_reference_batch(a, w)
     inst = _instance(w, a.seed)
     p = sd.maxcut_sdp(inst["weights"])
     times = []
@@ -162,6 +169,48 @@ def run_reference(a):
                                    f"{res.iters} iterations, median of {len(times)} solves"},
         "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "oracle_pobj": res.pobj,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _run_reference_batch(a, w):
+    """The oracle's dense IPM (O2) on the batch, one instance at a time. Each
+    step solves one instance of every order d present in the batch; the
+    batch's time is the sum over its 64 instances of the median time measured
+    for their order. At most two steps run (the order-11 solve alone takes
+    tens of seconds on the host)."""
+    from oracle import sdp_dense as sd
+    from paper_2509_11890_gb300 import inputs
+    insts = inputs.batch_maxcut(w["count"], a.seed, w["d_lo"], w["d_hi"])
+    rep = {}
+    for i in insts:
+        rep.setdefault(i["d"], i)
+    steps = min(max(a.steps, 1), 2)
+    times = {dd: [] for dd in rep}
+    for _ in range(steps):
+        for dd, i in sorted(rep.items()):
+            t0 = time.perf_counter()
+            sd.solve_dense(sd.maxcut_sdp(i["weights"]), tol=1e-4)
+            times[dd].append(time.perf_counter() - t0)
+    t_of = {dd: float(np.median(v)) for dd, v in times.items()}
+    per = [t_of[i["d"]] for i in insts]
+    total = float(sum(per))
+    val = len(insts) / total
+    desc = (f"dense HKM IPM (oracle O2) to relative gap 1e-4, one instance of each order d in {sorted(rep)} per "
+            f"step ({steps} steps); batch time = sum over the {len(insts)} instances of the median time of their "
+            f"order: {json.dumps({str(k): round(v, 4) for k, v in sorted(t_of.items())})} s")
+    line = {
+        "impl": "reference", "metric": "instances/s (batched time-to-gap-1e-4)", "value": val,
+        "unit": "instances/s", "n_gpus": a.gpus, "steps": steps, "warmup": a.warmup,
+        "ms_per_step": total * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "instances": w["count"], "d_range": [w["d_lo"], w["d_hi"]],
+                   "seed": a.seed},
+        "p50_time_to_gap_s": float(np.percentile(per, 50)), "p99_time_to_gap_s": float(np.percentile(per, 99)),
+        "cpu_baseline": {"value": val, "unit": "instances/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": val, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -304,10 +353,109 @@ def run_ours(a):
     return 0
 
 
+def run_batch(a):
+    """Batched solve: every step solves all instances of the batch concurrently
+    (tt_sdp_solve_batch: worker threads, one CUDA stream each); the value is
+    instances per second over the timed steps. Replicas shard nothing: under
+    torchrun every rank solves its own batch (seed + rank)."""
+    import torch
+
+    import paper_2509_11890_gb300 as tg
+    from paper_2509_11890_gb300 import inputs
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WORKLOADS[a.workload]
+    seed = replica_seed(a.seed, rank)
+    insts = inputs.batch_maxcut(w["count"], seed, w["d_lo"], w["d_hi"])
+    opts = tg.default_options(rank_cap=w["cap"], precision=PREC[a.precision], max_iters=60)
+
+    def make():
+        return [tg.Context.maxcut(i["adjacency_cores"], opts) for i in insts]
+
+    for _ in range(a.warmup):
+        # warm-up on a slice of the batch (one instance of every size)
+        seen, sub = set(), []
+        for i in insts:
+            if i["d"] not in seen:
+                seen.add(i["d"])
+                sub.append(tg.Context.maxcut(i["adjacency_cores"], opts))
+        tg.solve_batch(sub, workers=a.workers)
+        for c in sub:
+            c.close()
+    torch.cuda.synchronize()
+    l0 = tg.launch_count()
+    per, walls, results = [], [], []
+    with Clocks(local) as clk:
+        for _ in range(a.steps):
+            ctxs = make()
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            t0 = time.perf_counter()
+            res = tg.solve_batch(ctxs, workers=a.workers)
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - t0)
+            per += [r["seconds"] for r in res]
+            results = res
+            for c in ctxs:
+                c.close()
+    launches = tg.launch_count() - l0
+    wall = sum(walls)
+    wall, = max_over_ranks([wall], device="cuda")
+    n_inst = w["count"] * a.steps * world
+    conv = sum(r["status"] == 0 for r in results)
+    line = {
+        "metric": "instances/s (batched time-to-gap-1e-4)", "value": n_inst / wall, "unit": "instances/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": wall / a.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[a.precision],
+        "data": "synthetic",
+        "config": {"workload": a.workload, "instances": w["count"], "d_range": [w["d_lo"], w["d_hi"]],
+                   "d_values": [i["d"] for i in insts], "rank_cap": w["cap"], "seed": a.seed,
+                   "workers": a.workers, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "each instance streams its own cores; no flush"},
+        "p50_time_to_gap_s": float(np.percentile(per, 50)), "p99_time_to_gap_s": float(np.percentile(per, 99)),
+        "converged": int(conv), "iters_mean": float(np.mean([r["iters"] for r in results])),
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "roofline": None,
+        "e2e": {"value": n_inst / wall, "unit": "instances/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(64 * w["count"]),
+                "note": "contexts are created from host cores before the timed region; the step reads back "
+                        "one result record per instance"},
+    }
+    if rank == 0 and a.sequential > 0:
+        # one at a time in the plain FP64 form, on a bounded sample of the batch
+        o64 = tg.default_options(rank_cap=w["cap"], precision=0, max_iters=60)
+        sample = insts[: a.sequential]
+        ts = []
+        for i in sample:
+            c = tg.Context.maxcut(i["adjacency_cores"], o64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.solve()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            c.close()
+        line["sequential_fp64"] = {
+            "instances": len(sample), "instances_per_s": len(sample) / sum(ts),
+            "p50_time_to_gap_s": float(np.percentile(ts, 50)), "p99_time_to_gap_s": float(np.percentile(ts, 99)),
+            "sample": f"the first {len(sample)} instances of the batch, solved one after another in FP64"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if WORKLOADS[a.workload]["kind"] == "batch":
+        return run_batch(a)
     return run_ours(a)
 
 

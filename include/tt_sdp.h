@@ -147,6 +147,19 @@ tt_status tt_matvec(const tt_desc* op, const tt_desc* v, double* out, void* stre
  * result is written to *out (host) and the stream is synchronised. */
 tt_status tt_inner(const tt_desc* a, const tt_desc* b, double* out, void* stream);
 
+/* Row a12: the step-length eigenproblem (Section 2.2, Theorem "Optimal Step
+ * Size"; Section 3.4): lambda = min over TT vectors e of <e, dM e> / <e, M e>
+ * for symmetric TT matrices M (positive definite) and dM with equal square
+ * modes, device cores. Runs `sweeps` two-site DMRG sweeps (two_site = 1: at
+ * each bond the supercore's projected generalised eigenproblem, then a
+ * truncated SVD split with relative tolerance 1e-8 and at most `rank`, plus
+ * random kick columns up to `rank`) or one-site ALS sweeps (two_site = 0)
+ * from a random start of TT rank `rank` drawn from the SplitMix64 stream
+ * `seed`. The largest alpha with M + alpha dM positive semidefinite is
+ * -1/lambda when lambda < 0 and unbounded otherwise. FP64; synchronises. */
+tt_status tt_min_gen_eig(const tt_desc* M, const tt_desc* dM, int32_t rank, int32_t sweeps, int32_t two_site,
+                         uint64_t seed, double* lambda, void* stream);
+
 /* TT rounding (row a9; Oseledets' round_TT as used in Section 2.3):
  * right-to-left Householder QR, then left-to-right truncated SVD. Bond k
  * keeps the smallest rank whose discarded energy is <= (delta/sqrt(d-1))^2,
@@ -212,6 +225,8 @@ typedef struct {
                               larger ones matrix-free by restarted GMRES             */
   int32_t gmres_restart;
   int32_t gmres_max_iters; /* operator products per local solve                       */
+  int32_t eig_two_site;    /* step lengths (Section 3.4): 1 two-site DMRG sweeps with
+                              SVD rank adaptation and random kicks, 0 one-site ALS    */
 } tt_sdp_options;
 
 typedef struct tt_sdp_ctx tt_sdp_ctx;
@@ -226,6 +241,21 @@ typedef struct {
   int64_t gmres_iters; /* local GMRES operator products so far                       */
   int64_t pred_used;      /* bonds rounded by the predicted-rank range finder so far   */
   int64_t pred_fallbacks; /* predicted bonds that fell back to the adaptive SVD        */
+  /* Forcing check (Section 3.3, eq. forcing-condition, applied to the projected
+   * systems the AMEn sweep solves): the largest FP64 relative residual
+   * ||b - K x|| / ||b|| of a local solve in this iteration, K the projected
+   * operator with FP64 products, and the correction solves run so far because a
+   * residual exceeded the local tolerance (GMRES: eta/10, LU: 1e-10).        */
+  double forcing;
+  int64_t forcing_corrections;
+  /* Damp-and-retry (Section 3.5): updates redone with halved step lengths so
+   * far, because the next step-length solve found the iterate outside the
+   * cone (at most 4 per iteration; then TT_E_NOT_PD is returned).            */
+  int64_t damped_retries;
+  /* AHO -> XZ fallback (Section 3.5): AHO iterations redone with the XZ
+   * direction so far, because an AMEn solve missed its tolerance within the
+   * sweep budget or the admissible step was below 1e-3.                      */
+  int64_t xz_fallbacks;
 } tt_sdp_iter_info;
 
 typedef struct {
@@ -263,6 +293,19 @@ tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info);
 
 /* Iterates until the stopping rules hold or max_iters. */
 tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out);
+
+/* Solves n independent contexts concurrently: `workers` host threads, each
+ * with its own non-blocking CUDA stream on the current device, take contexts
+ * from a shared queue and run tt_sdp_solve on them (a context's own stream is
+ * replaced by the worker's for the duration). out[i] receives context i's
+ * result; out[i].seconds is its wall time from start to finish on its stream.
+ * The contexts must be distinct. A rank predictor may be attached to several
+ * of them (prediction only reads its parameters) but must not be trained
+ * while the batch runs. The tensor-core fault flag is one per device, so a
+ * fault in one context's kernel is reported by every context that reads it
+ * during the batch. Returns TT_OK when every context converged, else the
+ * status of the first context (by index) that did not. */
+tt_status tt_sdp_solve_batch(int32_t n, tt_sdp_ctx* const* ctxs, int32_t workers, tt_sdp_result* out);
 
 /* Copies iterate `which` (0 X, 1 Y, 2 T, 3 Z; TT matrices with 2 x 2 modes)
  * to the host. With cores == NULL only ranks (d+1 ints) and *count are set. */

@@ -375,7 +375,7 @@ def min_gen_eig(M: list, dM: list, e0: list | None, rnd: Counter, rank: int = 4,
         for k in order:
             Mk = _sym(envM.local_mat(k))
             Dk = _sym(envD.local_mat(k))
-            L = np.linalg.cholesky(Mk + 1e-300 * np.eye(len(Mk)))
+            L = _cholesky(Mk)
             Li = np.linalg.inv(L)
             S = _sym(Li @ Dk @ Li.T)
             w_, v_ = np.linalg.eigh(S)
@@ -413,6 +413,112 @@ def min_gen_eig(M: list, dM: list, e0: list | None, rnd: Counter, rank: int = 4,
     return lam, e
 
 
+def merge_op_cores(op: list, k: int) -> np.ndarray:
+    """Operator cores k and k+1 as one core with grouped modes [p][(i1 i2)][(j1 j2)][q]
+    (the two-site operator of a DMRG step, Section 3.4)."""
+    a, b = op[k], op[k + 1]
+    R, m1, n1, _ = a.shape
+    _, m2, n2, R2 = b.shape
+    c = np.tensordot(a, b, axes=([3], [0]))  # p i1 j1 i2 j2 q
+    return c.transpose(0, 1, 3, 2, 4, 5).reshape(R, m1 * m2, n1 * n2, R2)
+
+
+class NotPositiveDefinite(ArithmeticError):
+    """The iterate handed to the step-length eigenproblem is not positive definite (Section 3.4)."""
+
+
+def _cholesky(Mk: np.ndarray) -> np.ndarray:
+    try:
+        return np.linalg.cholesky(Mk)
+    except np.linalg.LinAlgError as e:
+        raise NotPositiveDefinite("step length: the projected iterate is not positive definite") from e
+
+
+def _local_gen_eig(Mk: np.ndarray, Dk: np.ndarray):
+    """Smallest eigenpair of Dk x = lam Mk x (Mk spd) through the Cholesky reduction."""
+    L = _cholesky(Mk)
+    Li = np.linalg.inv(L)
+    S = _sym(Li @ Dk @ Li.T)
+    w_, v_ = np.linalg.eigh(S)
+    return float(w_[0]), Li.T @ v_[:, 0]
+
+
+def dmrg_keep(s: np.ndarray, tol: float, cap: int) -> int:
+    """Smallest rank whose discarded tail energy is at most tol^2 of the total, in [1, cap]."""
+    tot = float(np.sum(s * s))
+    keep = len(s)
+    tail = 0.0
+    while keep > 1 and tail + s[keep - 1] ** 2 <= tol * tol * tot:
+        tail += s[keep - 1] ** 2
+        keep -= 1
+    return max(1, min(keep, cap))
+
+
+def min_gen_eig_dmrg(M: list, dM: list, e0: list | None, rnd: Counter, rank: int = 4, sweeps: int = 4,
+                     tol: float = 1e-8):
+    """min over TT vectors e of <e, dM e> / <e, M e> by two-site (DMRG) sweeps (Section 3.4).
+
+    The unknown at bond (k, k+1) is the supercore of cores k and k+1; its
+    projected generalised eigenproblem (with the merged operator cores) is
+    solved by the Cholesky reduction, and the supercore is split by a truncated
+    SVD (relative tolerance tol, at most `rank`). The orthonormal factor is then
+    enriched with random columns up to `rank` (the kick) and re-orthonormalised
+    by QR; the other factor is the projection of the supercore onto it.
+    Returns (lambda_min, e).
+    """
+    d = len(M)
+    if d < 2:
+        return min_gen_eig(M, dM, e0, rnd, rank, sweeps)
+    n = M[0].shape[1]
+    if e0 is None:
+        ranks = [1] + [min(rank, n ** min(k, d - k)) for k in range(1, d)] + [1]
+        e = [rnd.draw((ranks[k], n, ranks[k + 1])) for k in range(d)]
+    else:
+        e = [c.copy() for c in e0]
+    e = tt.orth_right(e)
+    envM = Env(M, None, d)
+    envD = Env(dM, None, d)
+    for k in range(d - 1, 1, -1):
+        envM.push_right(e, k)
+        envD.push_right(e, k)
+    Mm = [merge_op_cores(M, k) for k in range(d - 1)]
+    Dm = [merge_op_cores(dM, k) for k in range(d - 1)]
+    lam = math.inf
+    for sweep in range(sweeps):
+        forward = sweep % 2 == 0
+        bonds = range(d - 1) if forward else range(d - 2, -1, -1)
+        for k in bonds:
+            Mk = _sym(tt.local_matrix(envM.left[k], Mm[k], envM.right[k + 2]))
+            Dk = _sym(tt.local_matrix(envD.left[k], Dm[k], envD.right[k + 2]))
+            lam, x = _local_gen_eig(Mk, Dk)
+            rl, rr = e[k].shape[0], e[k + 1].shape[2]
+            mat = x.reshape(rl * n, n * rr)
+            U, sv, Vt = np.linalg.svd(mat, full_matrices=False)
+            keep = dmrg_keep(sv, tol, rank)
+            if forward:
+                left = U[:, :keep]
+                extra = min(rank, rl * n, n * rr) - keep
+                if extra > 0:
+                    q, _ = np.linalg.qr(np.concatenate([left, rnd.draw((rl * n, extra))], axis=1))
+                    left = q[:, :keep + extra]
+                e[k] = left.reshape(rl, n, left.shape[1])
+                e[k + 1] = (left.T @ mat).reshape(left.shape[1], n, rr)
+                envM.push_left(e, k)
+                envD.push_left(e, k)
+            else:
+                right = Vt[:keep].T  # (n rr) x keep, orthonormal columns
+                extra = min(rank, rl * n, n * rr) - keep
+                if extra > 0:
+                    q, _ = np.linalg.qr(np.concatenate([right, rnd.draw((n * rr, extra))], axis=1))
+                    right = q[:, :keep + extra]
+                e[k + 1] = right.T.reshape(right.shape[1], n, rr)
+                e[k] = (mat @ right).reshape(rl, n, right.shape[1])
+                envM.push_right(e, k + 1)
+                envD.push_right(e, k + 1)
+    e = tt.orth_right(e)
+    return lam, e
+
+
 def step_from_lambda(lam: float) -> float:
     """Theorem "Optimal Step Size": alpha = -1/lambda_min(M^-1/2 dM M^-1/2) when negative, else unbounded."""
     return math.inf if lam >= 0 else -1.0 / lam
@@ -438,6 +544,9 @@ class Options:
     seed: int = 1234
     eig_rank: int = 4
     eig_sweeps: int = 4
+    eig_two_site: bool = True   # two-site DMRG sweeps (Section 3.4); False: one-site ALS
+    max_retries: int = 4        # damp-and-retry of an update that left the cone (Section 3.5)
+    fallback_step: float = 1e-3  # AHO -> XZ fallback below this step length (Section 3.5)
 
 
 @dataclass
@@ -497,7 +606,7 @@ class TTIPM:
         if prob.A_ineq is not None:
             # X = lam I + (alpha_p / 10) A_ineq(J), T = lam_ineq A_ineq(J) (Section 5.1)
             aJ = prob.ones_t
-            lam_min, _ = min_gen_eig(I, aJ, None, self.rnd, rank=2, sweeps=6)
+            lam_min, _ = self._gen_eig(I, aJ, None, 2, 6)
             alpha_p = lam * step_from_lambda(lam_min) if lam_min < 0 else lam
             self.X = tt.add(tt.scale(I, lam), aJ, 1.0, alpha_p / 10.0)
             self.T = tt.scale(aJ, prob.lam0_ineq)
@@ -509,6 +618,9 @@ class TTIPM:
         self.w = None
         self.eX = self.eZ = self.eT = self.eS = None
         self.history = []
+        self.prev = None      # last update: iterate, direction, step lengths, rounding tolerances
+        self.retries = 0
+        self.fallbacks = 0
 
     # --- residuals and measures (Section 3.3, Section 3.5) ---
     def slack(self, X):
@@ -632,8 +744,13 @@ class TTIPM:
             a_p, a_d = min(a_p, a_s), min(a_d, a_t)
         return min(1.0, self.o.damping * a_p), min(1.0, self.o.damping * a_d)
 
+    def _gen_eig(self, M, dM, e0, rank, sweeps):
+        if self.o.eig_two_site:
+            return min_gen_eig_dmrg(M, dM, e0, self.rnd, rank, sweeps)
+        return min_gen_eig(M, dM, e0, self.rnd, rank, sweeps)
+
     def _max_step(self, M, dM, e0):
-        lam, e = min_gen_eig(M, _sym_tt(dM), e0, self.rnd, self.o.eig_rank, self.o.eig_sweeps)
+        lam, e = self._gen_eig(M, _sym_tt(dM), e0, self.o.eig_rank, self.o.eig_sweeps)
         return step_from_lambda(lam), e
 
     def _max_step_diag(self, v, dv, e0):
@@ -642,10 +759,37 @@ class TTIPM:
         p = self.p
         idle = tt.add(tt.vec_tt(tt.ones_mat(self.d)), tt.vec_tt(p.ones_t), 1.0, -1.0)
         M = tt.diag_tt(tt.add(v, idle))
-        lam, e = min_gen_eig(M, tt.diag_tt(dv), e0, self.rnd, 1, self.o.eig_sweeps)
+        lam, e = self._gen_eig(M, tt.diag_tt(dv), e0, 1, self.o.eig_sweeps)
         return step_from_lambda(lam), e
 
+    def _apply_update(self):
+        """Algorithm 1's update from the stored iterate, direction and step lengths,
+        rounded with the spectral shift (Corollary psdness_rounding)."""
+        u, cap = self.prev, self.o.rank_cap
+        self.X, _ = _round_psd(tt.add(u["X"], u["dX"], 1.0, u["ap"]), u["tol_p"], cap, self.I)
+        self.Z, _ = _round_psd(tt.add(u["Z"], u["dZ"], 1.0, u["ad"]), u["tol_d"], cap, self.I)
+        self.Y, _ = _round_psd(tt.add(u["Y"], u["dY"], 1.0, u["ad"]), u["tol_d"], cap, None)
+        if u["T"] is not None:
+            self.T, _ = _round_psd(tt.add(u["T"], u["dT"], 1.0, u["ad"]), u["tol_d"], cap, self.p.ones_t)
+
     def iterate(self, it: int) -> IterInfo | None:
+        """One iteration; an update that the next step-length solve finds outside
+        the cone is undone and repeated with both step lengths halved (the
+        damp-and-retry safeguard of Section 3.5), at most max_retries times."""
+        for attempt in range(self.o.max_retries + 1):
+            try:
+                return self._iterate_once(it)
+            except NotPositiveDefinite:
+                if self.prev is None or attempt == self.o.max_retries:
+                    raise
+                self.history.pop()
+                self.prev["ap"] *= 0.5
+                self.prev["ad"] *= 0.5
+                self._apply_update()
+                self.retries += 1
+        raise AssertionError("unreachable")
+
+    def _iterate_once(self, it: int) -> IterInfo | None:
         o, p = self.o, self.p
         rel_p, rel_d, rel_gap, pobj, dobj = self.measures()
         mu = self.mu()
@@ -659,8 +803,32 @@ class TTIPM:
         direction = "xz" if it < o.xz_warmup else "aho"
         zero_p = rel_p <= eps_p
         zero_d = rel_d <= eps_d
+        dX, dY, dT, dZ, ap, ad, sweeps, amen_ok = self._mehrotra(direction, mu, zero_p, zero_d)
+        if direction == "aho" and (min(ap, ad) < o.fallback_step or not amen_ok):
+            # Section 3.5: an AHO solve that misses its target within the rank and
+            # sweep budget, or whose admissible step is nearly zero, is redone
+            # with the XZ direction for this iteration
+            direction = "xz"
+            self.fallbacks += 1
+            dX, dY, dT, dZ, ap, ad, sweeps, amen_ok = self._mehrotra(direction, mu, zero_p, zero_d)
+        info.alpha_p, info.alpha_d, info.direction, info.sweeps = ap, ad, direction, sweeps
+        # update (Algorithm 1) and rounding with the spectral shift (Corollary psdness_rounding)
+        tol_p = self.eta * (1.0 + self.nB) / 10.0
+        tol_d = self.eta * (1.0 + self.nC) / 10.0
+        self.prev = dict(X=self.X, Y=self.Y, T=self.T, Z=self.Z, dX=dX, dY=dY, dT=dT, dZ=dZ, ap=ap, ad=ad,
+                         tol_p=tol_p, tol_d=tol_d)
+        self._apply_update()
+        info.ranks_X = tt.ranks(self.X)
+        info.ranks_Z = tt.ranks(self.Z)
+        return info
+
+    def _mehrotra(self, direction: str, mu: float, zero_p: bool, zero_d: bool):
+        """Mehrotra predictor and corrector solves and their step lengths (Section 3.5).
+        Returns the corrector direction, its step lengths, the AMEn sweeps of the
+        corrector and whether both AMEn solves met their tolerance."""
+        p = self.p
         # predictor
-        dXa, dYa, dTa, dZa, _ = self.direction(direction, 0.0, None, zero_p, zero_d)
+        dXa, dYa, dTa, dZa, pinfo = self.direction(direction, 0.0, None, zero_p, zero_d)
         ap, ad = self.steps(dXa, dTa, dZa)
         Xa = tt.add(self.X, dXa, 1.0, ap)
         Za = tt.add(self.Z, dZa, 1.0, ad)
@@ -675,19 +843,8 @@ class TTIPM:
             corr = (dXa, dZa, dTa, tt.matvec(p.A_ineq, tt.vec_tt(dXa)))
         dX, dY, dT, dZ, sinfo = self.direction(direction, sigma * mu, corr, zero_p, zero_d)
         ap, ad = self.steps(dX, dT, dZ)
-        info.alpha_p, info.alpha_d, info.direction, info.sweeps = ap, ad, direction, sinfo["sweeps"]
-        # update (Algorithm 1) and rounding with the spectral shift (Corollary psdness_rounding)
-        tol_p = self.eta * (1.0 + self.nB) / 10.0
-        tol_d = self.eta * (1.0 + self.nC) / 10.0
-        cap = o.rank_cap
-        self.X, _ = _round_psd(tt.add(self.X, dX, 1.0, ap), tol_p, cap, self.I)
-        self.Z, _ = _round_psd(tt.add(self.Z, dZ, 1.0, ad), tol_d, cap, self.I)
-        self.Y, _ = _round_psd(tt.add(self.Y, dY, 1.0, ad), tol_d, cap, None)
-        if self.T is not None:
-            self.T, _ = _round_psd(tt.add(self.T, dT, 1.0, ad), tol_d, cap, p.ones_t)
-        info.ranks_X = tt.ranks(self.X)
-        info.ranks_Z = tt.ranks(self.Z)
-        return info
+        amen_ok = pinfo["max_change"] < self.eta and sinfo["max_change"] < self.eta
+        return dX, dY, dT, dZ, ap, ad, sinfo["sweeps"], amen_ok
 
     def solve(self):
         for it in range(self.o.max_iters + 1):

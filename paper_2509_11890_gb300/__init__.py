@@ -157,6 +157,16 @@ def inner(a: DevTT, b: DevTT, stream=None) -> float:
     return res.value
 
 
+def min_gen_eig(M: DevTT, dM: DevTT, rank: int = 4, sweeps: int = 4, two_site: bool = True, seed: int = 1234,
+                stream=None) -> float:
+    """min over TT vectors e of <e, dM e>/<e, M e> (tt_min_gen_eig): the step-length eigenproblem."""
+    lam = ctypes.c_double(0.0)
+    a, b = M.desc(), dM.desc()
+    _check(lib().tt_min_gen_eig(ctypes.byref(a), ctypes.byref(b), int(rank), int(sweeps), int(bool(two_site)),
+                                int(seed), ctypes.byref(lam), _stream(stream)), "tt_min_gen_eig")
+    return lam.value
+
+
 def round_tt(a: DevTT, delta: float, cap: int = 0, stream=None):
     """TT rounding of the vector view of `a`; returns (DevTT, zeta)."""
     import torch
@@ -200,7 +210,10 @@ def tt_from_dense(dense, eps_rel=1e-13, cap=0, stream=None):
 def default_options(**kw) -> _lib.Options:
     o = _lib.Options()
     lib().tt_sdp_default_options(ctypes.byref(o))
+    names = {f for f, _ in _lib.Options._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
         setattr(o, k, v)
     return o
 
@@ -306,6 +319,17 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def solve_batch(contexts, workers=8):
+    """Solve independent contexts concurrently (tt_sdp_solve_batch); returns one result dict each."""
+    n = len(contexts)
+    handles = (ctypes.c_void_p * n)(*[c._h for c in contexts])
+    res = (_lib.Result * n)()
+    st = lib().tt_sdp_solve_batch(n, handles, workers, res)
+    if st not in (0, 7):
+        _check(st, "tt_sdp_solve_batch")
+    return [{f: getattr(r, f) for f, _ in _lib.Result._fields_} for r in res]
 
 
 class RankPredictor:

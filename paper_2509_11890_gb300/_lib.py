@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
                 ("eta0", c_double), ("eta_floor", c_double), ("eta_C", c_double), ("damping", c_double),
                 ("precision", c_int32), ("max_iters", c_int32), ("max_sweeps", c_int32), ("kick", c_int32),
                 ("eig_rank", c_int32), ("eig_sweeps", c_int32), ("seed", ctypes.c_uint64),
-                ("local_dense_max", c_int32), ("gmres_restart", c_int32), ("gmres_max_iters", c_int32)]
+                ("local_dense_max", c_int32), ("gmres_restart", c_int32), ("gmres_max_iters", c_int32),
+                ("eig_two_site", c_int32)]
 
 
 class IterInfo(ctypes.Structure):
@@ -43,7 +44,9 @@ class IterInfo(ctypes.Structure):
                 ("rel_d", c_double), ("rel_gap", c_double), ("pobj", c_double), ("dobj", c_double),
                 ("alpha_p", c_double), ("alpha_d", c_double), ("max_rank_X", c_int32), ("max_rank_Z", c_int32),
                 ("max_rank_W", c_int32), ("sweeps", c_int32), ("direction", c_int32), ("seconds", c_double),
-                ("gmres_iters", ctypes.c_int64), ("pred_used", ctypes.c_int64), ("pred_fallbacks", ctypes.c_int64)]
+                ("gmres_iters", ctypes.c_int64), ("pred_used", ctypes.c_int64), ("pred_fallbacks", ctypes.c_int64),
+                ("forcing", c_double), ("forcing_corrections", ctypes.c_int64), ("damped_retries", ctypes.c_int64),
+                ("xz_fallbacks", ctypes.c_int64)]
 
 
 class Result(ctypes.Structure):
@@ -67,6 +70,8 @@ SIGNATURES = {
     "tt_hadamard": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), c_void_p, c_void_p]),
     "tt_matvec": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), c_void_p, c_void_p]),
     "tt_inner": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), P_double, c_void_p]),
+    "tt_min_gen_eig": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(TTDesc), c_int32, c_int32, c_int32,
+                                 ctypes.c_uint64, P_double, c_void_p]),
     "tt_round": (c_int32, [ctypes.POINTER(TTDesc), c_double, c_int32, P_int32, c_void_p, c_size_t, P_double,
                            c_int32, c_void_p]),
     "tt_from_dense": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_int32, P_int32, c_void_p,
@@ -81,6 +86,7 @@ SIGNATURES = {
                                    ctypes.POINTER(Options), c_void_p, ctypes.POINTER(c_void_p)]),
     "tt_sdp_newton_step": (c_int32, [c_void_p, ctypes.POINTER(IterInfo)]),
     "tt_sdp_solve": (c_int32, [c_void_p, ctypes.POINTER(Result)]),
+    "tt_sdp_solve_batch": (c_int32, [c_int32, ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(Result)]),
     "tt_sdp_get_iterate": (c_int32, [c_void_p, c_int32, P_int32, c_void_p, ctypes.POINTER(c_size_t)]),
     "tt_sdp_order": (c_int32, [c_void_p]),
     "tt_sdp_destroy": (None, [c_void_p]),

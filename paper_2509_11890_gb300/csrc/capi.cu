@@ -102,6 +102,8 @@ Options to_options(const tt_sdp_options* o) {
   r.local_dense_max = o->local_dense_max;
   r.gmres_restart = o->gmres_restart;
   r.gmres_max_iters = o->gmres_max_iters;
+  r.eig_two_site = o->eig_two_site;
+  TT_CHECK(r.eig_two_site == 0 || r.eig_two_site == 1, TT_E_INVALID_ARG, "eig_two_site must be 0 or 1");
   TT_CHECK(r.local_dense_max >= 0 && r.gmres_restart > 0 && r.gmres_max_iters > 0, TT_E_INVALID_ARG,
            "invalid local solver options");
   TT_CHECK(r.rank_cap > 0 && r.max_sweeps > 0 && r.eig_sweeps > 0 && r.eig_rank > 0 && r.kick >= 0,
@@ -234,6 +236,21 @@ tt_status tt_inner(const tt_desc* a, const tt_desc* b, double* out, void* stream
   });
 }
 
+tt_status tt_min_gen_eig(const tt_desc* M, const tt_desc* dM, int32_t rank, int32_t sweeps, int32_t two_site,
+                         uint64_t seed, double* lambda, void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(lambda && rank > 0 && sweeps > 0 && (two_site == 0 || two_site == 1), TT_E_INVALID_ARG,
+             "bad tt_min_gen_eig arguments");
+    DTT a = desc_dev(M), b = desc_dev(dM);
+    TT_CHECK(a.d == b.d && a.m == b.m && a.n == b.n && a.m == a.n, TT_E_SHAPE,
+             "tt_min_gen_eig: M and dM must be square TT matrices with equal modes");
+    Counter rnd;
+    rnd.seed = seed;
+    *lambda = two_site ? min_gen_eig_dmrg(a, b, nullptr, false, rnd, rank, sweeps, TT_FP64, kDmrgTol)
+                       : min_gen_eig(a, b, nullptr, false, rnd, rank, sweeps, TT_FP64);
+  });
+}
+
 tt_status tt_round(const tt_desc* in, double delta, int32_t rank_cap, int32_t* ranks_out, double* cores_out,
                    size_t capacity, double* zeta_out, int32_t precision, void* stream) {
   return guarded(stream, [&] {
@@ -285,6 +302,7 @@ void tt_sdp_default_options(tt_sdp_options* o) {
   o->local_dense_max = 4096;
   o->gmres_restart = 40;
   o->gmres_max_iters = 400;
+  o->eig_two_site = 1;
 }
 
 static tt_status make_ctx(Problem p, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
@@ -387,6 +405,10 @@ tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info) {
     info->gmres_iters = l.gmres_iters;
     info->pred_used = l.pred_used;
     info->pred_fallbacks = l.pred_fallbacks;
+    info->forcing = l.forcing;
+    info->forcing_corrections = l.forcing_corrections;
+    info->damped_retries = l.retries;
+    info->xz_fallbacks = l.fallbacks;
   });
 }
 
@@ -564,3 +586,53 @@ tt_status tt_sdp_get_trace(tt_sdp_ctx* ctx, float* X, float* t, size_t* n) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// concurrent batch of independent solves
+// ---------------------------------------------------------------------------
+#include <atomic>
+#include <chrono>
+#include <thread>
+
+extern "C" tt_status tt_sdp_solve_batch(int32_t n, tt_sdp_ctx* const* ctxs, int32_t workers, tt_sdp_result* out) {
+  if (n < 0 || (n > 0 && (!ctxs || !out)) || workers <= 0) return TT_E_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return TT_E_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TT_E_CUDA;
+  for (int i = 0; i < n; ++i) cudaStreamSynchronize(ctxs[i]->stream);  // creation work is complete
+  std::atomic<int> next{0};
+  std::vector<tt_status> st(n, TT_OK);
+  std::vector<std::thread> pool;
+  const int nw = workers < n ? workers : (n > 0 ? n : 1);
+  for (int w = 0; w < nw; ++w) {
+    pool.emplace_back([&]() {
+      cudaSetDevice(dev);
+      cudaStream_t s = nullptr;
+      const bool have_stream = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+      for (;;) {
+        const int i = next.fetch_add(1);
+        if (i >= n) break;
+        if (!have_stream) {
+          st[i] = TT_E_CUDA;
+          continue;
+        }
+        cudaStream_t own = ctxs[i]->stream;
+        ctxs[i]->stream = s;
+        const auto t0 = std::chrono::steady_clock::now();
+        st[i] = tt_sdp_solve(ctxs[i], &out[i]);
+        cudaStreamSynchronize(s);
+        out[i].seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        ctxs[i]->stream = own;
+      }
+      if (have_stream) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    });
+  }
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < n; ++i)
+    if (st[i] != TT_OK) return st[i];
+  return TT_OK;
+}

@@ -3,10 +3,13 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <ctime>
 #include <cstdio>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -82,12 +85,12 @@ class DBuf {
 
 // Counts kernel launches issued by the library (reported by the benchmark).
 struct LaunchCounter {
-  static unsigned long long& value() {
-    static unsigned long long v = 0;
+  static std::atomic<unsigned long long>& value() {
+    static std::atomic<unsigned long long> v{0};
     return v;
   }
 };
-inline void count_launch() { ++LaunchCounter::value(); }
+inline void count_launch() { LaunchCounter::value().fetch_add(1, std::memory_order_relaxed); }
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 
@@ -108,6 +111,8 @@ struct Profiler {
     return t;
   }
   static void add(const char* name, double s) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
     for (auto& p : table())
       if (p.first == name) {
         p.second += s;

@@ -339,6 +339,16 @@ Stats& stats(int key) {
   static Stats s[2];
   return s[key & 1];
 }
+// the event pair a thread has opened and not yet closed, per key (threads that
+// solve contexts concurrently each time their own contractions)
+struct OpenPair {
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  bool open = false;
+};
+OpenPair& open_pair(int key) {
+  static thread_local OpenPair o[2];
+  return o[key & 1];
+}
 void resolve(Stats& s) {
   for (auto& ev : s.pending) {
     TT_CUDA(cudaEventSynchronize(ev.second));
@@ -362,15 +372,21 @@ void stats_begin(cudaStream_t st, int key) {
     TT_CUDA(cudaEventCreate(&ev.first));
     TT_CUDA(cudaEventCreate(&ev.second));
   }
+  OpenPair& o = open_pair(key);
+  if (o.open) s.pool.push_back(o.ev);  // a begin without an end (an exception in between)
   TT_CUDA(cudaEventRecord(ev.first, st));
-  s.pending.push_back(ev);
+  o.ev = ev;
+  o.open = true;
 }
 
 void stats_end(cudaStream_t st, double flops, int key) {
   Stats& s = stats(key);
   std::lock_guard<std::mutex> lk(s.mu);
-  if (s.pending.empty()) return;
-  TT_CUDA(cudaEventRecord(s.pending.back().second, st));
+  OpenPair& o = open_pair(key);
+  if (!o.open) return;
+  TT_CUDA(cudaEventRecord(o.ev.second, st));
+  o.open = false;
+  s.pending.push_back(o.ev);
   s.flops += flops;
   ++s.calls;
   if (s.pending.size() > 4096) resolve(s);

@@ -6,6 +6,7 @@
 // local systems is blocked so that its trailing updates use the multi-CTA
 // strided GEMM.
 #include <cfloat>
+#include <mutex>
 
 #include "gemm.cuh"
 #include "linalg.cuh"
@@ -16,6 +17,8 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+// dynamic shared memory the Jacobi SVD may use for its working columns
+constexpr size_t kJacobiSmem = 200 * 1024;
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -49,24 +52,25 @@ __device__ __forceinline__ float eps_of<float>() { return FLT_EPSILON; }
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) qr_kernel(MatView<T> A, T* W, T* tau, T* Q, T* R) {
+  // W holds A column-major (W[c*m + i]) so that every column operation below
+  // reads consecutive addresses across a warp; Q is formed column-major in
+  // the first m*k entries of W's companion buffer Q and transposed at the end
   __shared__ T red[kWarps];
   __shared__ T s_beta, s_tau, s_scale;
   const int m = A.m, n = A.n, k = m < n ? m : n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (long long idx = tid; idx < (long long)m * n; idx += kThreads) {
-    int i = (int)(idx / n), j = (int)(idx % n);
-    W[idx] = A.p[i * A.rs + j * A.cs];
+    int c = (int)(idx / m), i = (int)(idx % m);
+    W[idx] = A.p[i * A.rs + c * A.cs];
   }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
+    T* wj = W + (long long)j * m;
     T loc = T(0);
-    for (int i = j + 1 + tid; i < m; i += kThreads) {
-      T x = W[(long long)i * n + j];
-      loc += x * x;
-    }
+    for (int i = j + 1 + tid; i < m; i += kThreads) loc += wj[i] * wj[i];
     T sigma = block_sum(loc, red);
     if (tid == 0) {
-      T alpha = W[(long long)j * n + j];
+      T alpha = wj[j];
       if (sigma == T(0)) {
         s_tau = T(0);
         s_beta = alpha;
@@ -81,46 +85,58 @@ __global__ void __launch_bounds__(kThreads) qr_kernel(MatView<T> A, T* W, T* tau
       tau[j] = s_tau;
     }
     __syncthreads();
-    for (int i = j + 1 + tid; i < m; i += kThreads) W[(long long)i * n + j] *= s_scale;
+    for (int i = j + 1 + tid; i < m; i += kThreads) wj[i] *= s_scale;
     __syncthreads();
-    if (tid == 0) W[(long long)j * n + j] = s_beta;
+    if (tid == 0) wj[j] = s_beta;
     const T tj = s_tau;
     if (tj != T(0)) {
       for (int c = j + 1 + warp; c < n; c += kWarps) {
+        T* wc = W + (long long)c * m;
         T dot = T(0);
-        for (int i = j + 1 + lane; i < m; i += 32) dot += W[(long long)i * n + j] * W[(long long)i * n + c];
+        for (int i = j + 1 + lane; i < m; i += 32) dot += wj[i] * wc[i];
         dot = warp_sum(dot);
-        dot += W[(long long)j * n + c];
+        dot += wc[j];
         T f = tj * dot;
-        if (lane == 0) W[(long long)j * n + c] -= f;
-        for (int i = j + 1 + lane; i < m; i += 32) W[(long long)i * n + c] -= f * W[(long long)i * n + j];
+        if (lane == 0) wc[j] -= f;
+        for (int i = j + 1 + lane; i < m; i += 32) wc[i] -= f * wj[i];
       }
     }
     __syncthreads();
   }
   for (long long idx = tid; idx < (long long)k * n; idx += kThreads) {
     int i = (int)(idx / n), c = (int)(idx % n);
-    R[idx] = c >= i ? W[(long long)i * n + c] : T(0);
+    R[idx] = c >= i ? W[(long long)c * m + i] : T(0);
   }
+  // Q column-major in Qc = Q (m*k entries), then transposed in place through W
+  T* Qc = Q;
   for (long long idx = tid; idx < (long long)m * k; idx += kThreads) {
-    int i = (int)(idx / k), c = (int)(idx % k);
-    Q[idx] = i == c ? T(1) : T(0);
+    int c = (int)(idx / m), i = (int)(idx % m);
+    Qc[idx] = i == c ? T(1) : T(0);
   }
   __syncthreads();
   for (int j = k - 1; j >= 0; --j) {
     const T tj = tau[j];
+    const T* wj = W + (long long)j * m;
     if (tj != T(0)) {
       for (int c = j + warp; c < k; c += kWarps) {
+        T* qc = Qc + (long long)c * m;
         T dot = T(0);
-        for (int i = j + 1 + lane; i < m; i += 32) dot += W[(long long)i * n + j] * Q[(long long)i * k + c];
+        for (int i = j + 1 + lane; i < m; i += 32) dot += wj[i] * qc[i];
         dot = warp_sum(dot);
-        dot += Q[(long long)j * k + c];
+        dot += qc[j];
         T f = tj * dot;
-        if (lane == 0) Q[(long long)j * k + c] -= f;
-        for (int i = j + 1 + lane; i < m; i += 32) Q[(long long)i * k + c] -= f * W[(long long)i * n + j];
+        if (lane == 0) qc[j] -= f;
+        for (int i = j + 1 + lane; i < m; i += 32) qc[i] -= f * wj[i];
       }
     }
     __syncthreads();
+  }
+  // the reflectors are no longer needed: stage Q^T-layout through W
+  for (long long idx = tid; idx < (long long)m * k; idx += kThreads) W[idx] = Qc[idx];
+  __syncthreads();
+  for (long long idx = tid; idx < (long long)m * k; idx += kThreads) {
+    int i = (int)(idx / k), c = (int)(idx % k);
+    Q[idx] = W[(long long)c * m + i];
   }
 }
 
@@ -129,12 +145,17 @@ __global__ void __launch_bounds__(kThreads) qr_kernel(MatView<T> A, T* W, T* tau
 // stored contiguously; round-robin ordering so each round's pairs are disjoint.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transposed, T* Wc, T* Vc,
-                                                       T* U, T* S, T* Vt, int* perm) {
+__global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transposed, T* Wg, T* Vg, bool w_smem,
+                                                       bool v_smem, T* U, T* S, T* Vt, int* perm) {
   __shared__ int s_rot;
+  // the working columns live in shared memory when they fit (every rotation
+  // then costs shared-memory latency instead of an L2 round trip)
+  extern __shared__ __align__(16) unsigned char jac_smem[];
   // work on B = A (m x n, m >= n) or B = A^T when A is wide
   const int m = transposed ? A.n : A.m;
   const int n = transposed ? A.m : A.n;
+  T* Wc = w_smem ? reinterpret_cast<T*>(jac_smem) : Wg;
+  T* Vc = v_smem ? reinterpret_cast<T*>(jac_smem) + (w_smem ? (size_t)m * n : 0) : Vg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (long long idx = tid; idx < (long long)m * n; idx += kThreads) {
     int j = (int)(idx / m), i = (int)(idx % m);  // column j, row i of B
@@ -319,9 +340,9 @@ __global__ void __launch_bounds__(kThreads) lu_panel_kernel(int n, T* A, T* b, i
 
 template <typename T>
 __global__ void lu_swap_trsm_kernel(int n, T* A, T* b, int j0, int jb, const int* ipiv) {
-  // one thread per column outside the panel (and the right-hand side)
+  // one thread per column outside the panel (and the right-hand side, if any)
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int ncols = n - jb + 1;
+  int ncols = n - jb + (b ? 1 : 0);
   if (c >= ncols) return;
   int col = c < j0 ? c : c + jb;  // skip the panel columns; col == n means b
   auto at = [&](int i) -> T& { return col < n ? A[(long long)i * n + col] : b[i]; };
@@ -343,30 +364,88 @@ __global__ void lu_swap_trsm_kernel(int n, T* A, T* b, int j0, int jb, const int
   }
 }
 
+// Forward and backward substitution with the factors of lu_factor for one
+// right-hand side: the row interchanges, then unit-lower and upper solves in
+// blocks of 32 rows (the off-block part of each row is a warp dot product
+// over a contiguous row segment, the 32 x 32 triangle runs in one warp).
+// x lives in shared memory when it fits, else in b itself.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) upper_solve_kernel(int n, const T* A, T* b) {
-  __shared__ T s_x;
-  for (int i = n - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) {
-      T d = A[(long long)i * n + i];
-      s_x = d != T(0) ? b[i] / d : T(0);
-      b[i] = s_x;
+__global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* A, const int* ipiv, T* b,
+                                                            bool use_smem) {
+  extern __shared__ __align__(16) unsigned char lu_smem[];
+  T* x = use_smem ? reinterpret_cast<T*>(lu_smem) : b;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (use_smem)
+    for (int i = tid; i < n; i += kThreads) x[i] = b[i];
+  __syncthreads();
+  if (tid == 0)
+    for (int j = 0; j < n; ++j) {
+      const int p = ipiv[j];
+      if (p != j) {
+        T t = x[j];
+        x[j] = x[p];
+        x[p] = t;
+      }
+    }
+  __syncthreads();
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int ib = n - i0 < 32 ? n - i0 : 32;
+    for (int r = warp; r < ib; r += kWarps) {
+      const T* row = A + (long long)(i0 + r) * n;
+      T s = T(0);
+      for (int t = lane; t < i0; t += 32) s += row[t] * x[t];
+      s = warp_sum(s);
+      if (lane == 0) x[i0 + r] -= s;
     }
     __syncthreads();
-    T x = s_x;
-    for (int j = threadIdx.x; j < i; j += kThreads) b[j] -= A[(long long)j * n + i] * x;
+    if (warp == 0) {
+      for (int r = 1; r < ib; ++r) {
+        const T* row = A + (long long)(i0 + r) * n + i0;
+        T s = lane < r ? row[lane] * x[i0 + lane] : T(0);
+        s = warp_sum(s);
+        if (lane == 0) x[i0 + r] -= s;
+        __syncwarp();
+      }
+    }
     __syncthreads();
   }
+  for (int i1 = n; i1 > 0; i1 -= 32) {
+    const int i0 = i1 - 32 > 0 ? i1 - 32 : 0, ib = i1 - i0;
+    for (int r = warp; r < ib; r += kWarps) {
+      const T* row = A + (long long)(i0 + r) * n;
+      T s = T(0);
+      for (int t = i1 + lane; t < n; t += 32) s += row[t] * x[t];
+      s = warp_sum(s);
+      if (lane == 0) x[i0 + r] -= s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int r = ib - 1; r >= 0; --r) {
+        const T* row = A + (long long)(i0 + r) * n + i0;
+        T s = (lane > r && lane < ib) ? row[lane] * x[i0 + lane] : T(0);
+        s = warp_sum(s);
+        if (lane == 0) {
+          const T dg = row[r];
+          x[i0 + r] = dg != T(0) ? (x[i0 + r] - s) / dg : T(0);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  if (use_smem)
+    for (int i = tid; i < n; i += kThreads) b[i] = x[i];
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) cholesky_kernel(int n, T* A) {
+__global__ void __launch_bounds__(kThreads) cholesky_kernel(int n, T* A, int* nonpos) {
   __shared__ T s_d;
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
       T v = A[(long long)j * n + j];
       s_d = v > T(0) ? sqrt(v) : T(0);
       A[(long long)j * n + j] = s_d;
+      if (!(v > T(0)) && nonpos) *nonpos = 1;
     }
     __syncthreads();
     T d = s_d;
@@ -449,45 +528,67 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st) {
   }
   bool tr = A.m < A.n;
   int m = tr ? A.n : A.m, n = tr ? A.m : A.n;
-  DBuf<T> Wc((size_t)m * n), Vc((size_t)n * n);
+  static std::once_flag attr_once;
+  cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&]() {
+    attr_err = cudaFuncSetAttribute(svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmem);
+  });
+  TT_CUDA(attr_err);
+  const size_t wb = (size_t)m * n * sizeof(T), vb = (size_t)n * n * sizeof(T);
+  const bool w_smem = wb <= kJacobiSmem;
+  const bool v_smem = w_smem && wb + vb <= kJacobiSmem;
+  const size_t smem = (w_smem ? wb : 0) + (v_smem ? vb : 0);
+  DBuf<T> Wc(w_smem ? 0 : (size_t)m * n), Vc(v_smem ? 0 : (size_t)n * n);
   DBuf<int> perm((size_t)n);
-  svd_kernel<T><<<1, kThreads, 0, st>>>(A, tr, Wc.get(), Vc.get(), U, S, Vt, perm.get());
+  svd_kernel<T><<<1, kThreads, smem, st>>>(A, tr, Wc.get(), Vc.get(), w_smem, v_smem, U, S, Vt, perm.get());
   count_launch();
   check_launch("svd_kernel");
 }
 
 template <typename T>
-void lu_solve(int n, T* A, T* b, cudaStream_t st) {
+void lu_factor(int n, T* A, int* ipiv, cudaStream_t st) {
   if (n <= 0) return;
   constexpr int nb = 32;
-  DBuf<int> ipiv((size_t)n);
   for (int j0 = 0; j0 < n; j0 += nb) {
     int jb = n - j0 < nb ? n - j0 : nb;
-    lu_panel_kernel<T><<<1, kThreads, 0, st>>>(n, A, b, j0, jb, ipiv.get());
+    lu_panel_kernel<T><<<1, kThreads, 0, st>>>(n, A, nullptr, j0, jb, ipiv);
     count_launch();
-    int ncols = n - jb + 1;
-    lu_swap_trsm_kernel<T><<<ceil_div(ncols, 128), 128, 0, st>>>(n, A, b, j0, jb, ipiv.get());
-    count_launch();
+    int ncols = n - jb;
+    if (ncols > 0) {
+      lu_swap_trsm_kernel<T><<<ceil_div(ncols, 128), 128, 0, st>>>(n, A, nullptr, j0, jb, ipiv);
+      count_launch();
+    }
     int rest = n - j0 - jb;
-    if (rest > 0) {
-      // A22 -= A21 A12 ; b2 -= A21 b1
+    if (rest > 0)
       gemm_rm<T>(false, false, rest, rest, jb, T(-1), A + (long long)(j0 + jb) * n + j0, n, 0,
                  A + (long long)j0 * n + j0 + jb, n, 0, T(1), A + (long long)(j0 + jb) * n + j0 + jb, n,
                  0, 1, st);
-      gemm_rm<T>(false, false, rest, 1, jb, T(-1), A + (long long)(j0 + jb) * n + j0, n, 0, b + j0, 1,
-                 0, T(1), b + j0 + jb, 1, 0, 1, st);
-    }
   }
-  check_launch("lu");
-  upper_solve_kernel<T><<<1, kThreads, 0, st>>>(n, A, b);
-  count_launch();
-  check_launch("upper_solve");
+  check_launch("lu_factor");
 }
 
 template <typename T>
-void cholesky_lower(int n, T* A, cudaStream_t st) {
+void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st) {
   if (n <= 0) return;
-  cholesky_kernel<T><<<1, kThreads, 0, st>>>(n, A);
+  constexpr size_t kMaxSmem = 48 * 1024;  // default dynamic shared-memory limit
+  const bool use_smem = (size_t)n * sizeof(T) <= kMaxSmem;
+  lu_apply_kernel<T><<<1, kThreads, use_smem ? (size_t)n * sizeof(T) : 0, st>>>(n, LU, ipiv, b, use_smem);
+  count_launch();
+  check_launch("lu_apply_kernel");
+}
+
+template <typename T>
+void lu_solve(int n, T* A, T* b, cudaStream_t st) {
+  if (n <= 0) return;
+  DBuf<int> ipiv((size_t)n);
+  lu_factor<T>(n, A, ipiv.get(), st);
+  lu_solve_factored<T>(n, A, ipiv.get(), b, st);
+}
+
+template <typename T>
+void cholesky_lower(int n, T* A, cudaStream_t st, int* nonpos) {
+  if (n <= 0) return;
+  cholesky_kernel<T><<<1, kThreads, 0, st>>>(n, A, nonpos);
   count_launch();
   check_launch("cholesky");
 }
@@ -515,7 +616,9 @@ void transpose(int m, int n, const T* in, T* out, cudaStream_t st) {
   template void qr_thin<T>(MatView<T>, T*, T*, cudaStream_t);                   \
   template void svd_thin<T>(MatView<T>, T*, T*, T*, cudaStream_t);              \
   template void lu_solve<T>(int, T*, T*, cudaStream_t);                         \
-  template void cholesky_lower<T>(int, T*, cudaStream_t);                       \
+  template void lu_factor<T>(int, T*, int*, cudaStream_t);                      \
+  template void lu_solve_factored<T>(int, const T*, const int*, T*, cudaStream_t); \
+  template void cholesky_lower<T>(int, T*, cudaStream_t, int*);                 \
   template void tri_lower_inverse<T>(int, T*, cudaStream_t);                    \
   template void transpose<T>(int, int, const T*, T*, cudaStream_t);
 INST(double)

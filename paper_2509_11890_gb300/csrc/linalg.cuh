@@ -30,10 +30,19 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st);
 template <typename T>
 void lu_solve(int n, T* A, T* b, cudaStream_t st);
 
+// The two halves of lu_solve: lu_factor overwrites A with its unit-lower L
+// and upper U factors (P A = L U, row interchanges in ipiv, n entries);
+// lu_solve_factored then solves A x = b in place for one right-hand side
+// and may be called any number of times on the same factors.
+template <typename T>
+void lu_factor(int n, T* A, int* ipiv, cudaStream_t st);
+template <typename T>
+void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st);
+
 // Lower Cholesky factor in place (row-major n x n; upper part zeroed) and
 // the inverse of a lower triangular matrix in place. Single CTA.
 template <typename T>
-void cholesky_lower(int n, T* A, cudaStream_t st);
+void cholesky_lower(int n, T* A, cudaStream_t st, int* nonpos = nullptr);  // *nonpos = 1 on a pivot <= 0
 template <typename T>
 void tri_lower_inverse(int n, T* L, cudaStream_t st);
 

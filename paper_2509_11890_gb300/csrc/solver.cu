@@ -8,8 +8,10 @@
 // Corollary psdness_rounding.
 #include <algorithm>
 #include <cmath>
+#include <exception>
 #include <functional>
 #include <limits>
+#include <thread>
 
 #include "contract.cuh"
 #include "gemm.cuh"
@@ -20,6 +22,63 @@
 namespace ttsdp {
 
 namespace {
+
+// Runs independent jobs concurrently: job 0 on the calling thread and stream,
+// job i > 0 on its own host thread and on side stream i-1, which first waits
+// for everything already queued on the calling stream. The calling stream
+// then waits for every side stream. The first exception is rethrown after all
+// jobs have ended and their streams are drained.
+void run_concurrently(std::vector<std::function<void()>>& jobs, std::vector<cudaStream_t>& side) {
+  if (jobs.empty()) return;
+  if (jobs.size() == 1) {
+    jobs[0]();
+    return;
+  }
+  cudaStream_t main = cur_stream();
+  int dev = 0;
+  TT_CUDA(cudaGetDevice(&dev));
+  while (side.size() + 1 < jobs.size()) {
+    cudaStream_t s = nullptr;
+    TT_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    side.push_back(s);
+  }
+  cudaEvent_t start = nullptr;
+  TT_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  TT_CUDA(cudaEventRecord(start, main));
+  const size_t nj = jobs.size();
+  std::vector<cudaEvent_t> done(nj, nullptr);
+  std::vector<std::exception_ptr> err(nj);
+  for (size_t i = 1; i < nj; ++i) TT_CUDA(cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming));
+  std::vector<std::thread> th;
+  for (size_t i = 1; i < nj; ++i) {
+    cudaStream_t s = side[i - 1];
+    th.emplace_back([&, i, s]() {
+      try {
+        TT_CUDA(cudaSetDevice(dev));
+        StreamScope::current() = s;
+        TT_CUDA(cudaStreamWaitEvent(s, start, 0));
+        jobs[i]();
+        TT_CUDA(cudaEventRecord(done[i], s));
+      } catch (...) {
+        err[i] = std::current_exception();
+        cudaStreamSynchronize(s);
+      }
+    });
+  }
+  try {
+    jobs[0]();
+  } catch (...) {
+    err[0] = std::current_exception();
+  }
+  for (auto& t : th) t.join();
+  for (size_t i = 1; i < nj; ++i) {
+    cudaStreamWaitEvent(main, done[i], 0);
+    cudaEventDestroy(done[i]);
+  }
+  cudaEventDestroy(start);
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
+}
 
 // ---------------------------------------------------------------------------
 // environments of <W, Op V>
@@ -148,30 +207,52 @@ void svd_prec(int prec, MatView<double> A, double* U, double* S, double* Vt, cud
 
 // Dense local solve K x = b (K destroyed, b becomes x). The mixed precisions
 // factor in FP32 and refine the solution twice against the FP64 residual.
-void lu_solve_prec(int prec, int N, double* K, double* b) {
+// FP64 relative residual at which the refinement of a dense local solve stops
+// (the accuracy of an FP64 LU of the projected system)
+constexpr double kLuRefineTol = 1e-10;
+
+// Solves K x = b (K N x N row-major FP64, kept; b becomes x) and returns the
+// FP64 relative residual ||b - K x|| / ||b|| of the returned x. FP64: LU of
+// a copy. Mixed modes: one FP32 LU, then FP64 iterative refinement whose
+// correction solves reuse the factors, until the FP64 residual is at most
+// ftol ||b|| or five corrections have run.
+double lu_solve_prec(int prec, int N, double* K, double* b, double ftol, int* corrections) {
   cudaStream_t st = cur_stream();
-  if (prec == TT_FP64) {
-    lu_solve<double>(N, K, b, st);
-    return;
-  }
   const size_t nn = (size_t)N * N;
-  DBuf<float> kf(nn), rf(N);
+  const double bnorm = dev_norm(b, N);
   DBuf<double> x(N), r(N);
-  dev_fill(x.get(), N, 0.0, st);
-  dev_copy(r.get(), b, N, st);
-  for (int it = 0; it < 3; ++it) {
-    to_f32(K, kf.get(), nn, st);
-    to_f32(r.get(), rf.get(), N, st);
-    lu_solve<float>(N, kf.get(), rf.get(), st);
-    DBuf<double> dx(N);
-    to_f64(rf.get(), dx.get(), N, st);
-    dev_axpy(x.get(), dx.get(), N, 1.0, st);
-    if (it == 2) break;
-    // r = b - K x in FP64
+  auto residual = [&]() {
     dev_copy(r.get(), b, N, st);
     gemm_rm<double>(false, false, N, 1, N, -1.0, K, N, 0, x.get(), 1, 0, 1.0, r.get(), 1, 0, 1, st);
+    return bnorm > 0 ? dev_norm(r.get(), N) / bnorm : 0.0;
+  };
+  double rho = 0.0;
+  if (prec == TT_FP64) {
+    DBuf<double> Kc(nn);
+    dev_copy(Kc.get(), K, nn, st);
+    dev_copy(x.get(), b, N, st);
+    lu_solve<double>(N, Kc.get(), x.get(), st);
+    rho = residual();
+  } else {
+    DBuf<float> kf(nn), rf(N);
+    DBuf<int> ipiv(N);
+    DBuf<double> dx(N);
+    dev_fill(x.get(), N, 0.0, st);
+    dev_copy(r.get(), b, N, st);
+    to_f32(K, kf.get(), nn, st);
+    lu_factor<float>(N, kf.get(), ipiv.get(), st);
+    for (int it = 0; it < 5; ++it) {
+      to_f32(r.get(), rf.get(), N, st);
+      lu_solve_factored<float>(N, kf.get(), ipiv.get(), rf.get(), st);
+      to_f64(rf.get(), dx.get(), N, st);
+      dev_axpy(x.get(), dx.get(), N, 1.0, st);
+      if (corrections && it > 0) ++*corrections;
+      rho = residual();
+      if (rho <= ftol) break;
+    }
   }
   dev_copy(b, x.get(), N, st);
+  return rho;
 }
 
 // ---------------------------------------------------------------------------
@@ -200,6 +281,8 @@ struct AmenInfo {
   int sweeps = 0;
   double max_change = 0.0;
   long long gmres_iters = 0;
+  double forcing = 0.0;        // largest FP64 relative residual of a local solve
+  long long corrections = 0;   // correction solves the forcing check asked for
 };
 
 // Restarted GMRES (Saad & Schultz) on device vectors with classical
@@ -281,8 +364,28 @@ int gmres(size_t N, const std::function<void(const double*, double*)>& A, const 
   return total;
 }
 
+// Relative change of the local blocks below which sweeps in a reduced
+// precision have converged as far as that precision allows: four unit
+// roundoffs of the contraction input format.
+double sweep_floor(int prec) {
+  switch (prec) {
+    case TT_FP32: return 4.0 * 5.96e-8;        // 2^-24
+    case TT_MIXED_TF32: return 4.0 * 4.88e-4;  // 2^-11
+    case TT_MIXED_BF16: return 4.0 * 3.91e-3;  // 2^-8
+    default: return 0.0;
+  }
+}
+
+// FP64 sweeps that refine a direction found in a reduced precision
+constexpr int kRefineSweeps = 2;
+
 BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap, int kick, int max_sweeps,
-                   Counter& rnd, int prec, int dense_max, int gmres_restart, int gmres_maxit, AmenInfo* info) {
+                   Counter& rnd, int prec_in, int dense_max, int gmres_restart, int gmres_maxit, AmenInfo* info) {
+  // sweeps run in prec_in until they stall at its floor (or use the sweep
+  // budget), then up to kRefineSweeps FP64 sweeps refine the direction with
+  // FP64 environments, local operators and solves
+  int prec = prec_in;
+  int refine = 0;
   const int nblk = nd.nblk();
   cudaStream_t st = cur_stream();
   BlockTT w = w0 ? *w0 : init_block(d, nblk, kick, rnd);
@@ -320,7 +423,8 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
   std::vector<int> blockshape = {frame.r[0], 4, frame.r[1]};
   int sweep = 0;
   double max_change = 0.0;
-  for (sweep = 0; sweep < max_sweeps; ++sweep) {
+  const int budget = max_sweeps + (prec_in != TT_FP64 ? kRefineSweeps : 0);
+  for (sweep = 0; sweep < budget; ++sweep) {
     const bool forward = sweep % 2 == 0;
     max_change = 0.0;
     for (int step = 0; step < d; ++step) {
@@ -336,12 +440,13 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         // matrix-free reduced system (eq. reduced_kkt_system) solved by GMRES:
         // each block product inserts the vector into core k and contracts it
         // with the cached environments and the operator core
+        int mv_prec = prec;  // precision of the block products (FP64 for the forcing check)
         auto apply_sum = [&](std::vector<Env>& es, const double* x, double* y, double scale, bool acc) {
           DBuf<double> tmp(n);
           if (!acc) dev_fill(y, n, 0.0, st);
           for (Env& e : es) {
             CDims c{rl, rr, e.op.r[k], e.op.r[k + 1], rl, rr, e.op.m, e.op.n};
-            local_apply(c, e.L[k].get(), e.op.core(k), e.R[k + 1].get(), x, tmp.get(), prec, st);
+            local_apply(c, e.L[k].get(), e.op.core(k), e.R[k + 1].get(), x, tmp.get(), mv_prec, st);
             dev_axpy(y, tmp.get(), n, scale, st);
           }
         };
@@ -373,6 +478,30 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         if (blockshape[0] == rl && blockshape[2] == rr && block) dev_copy(x.get(), block->get(), N, st);
         else dev_fill(x.get(), N, 0.0, st);
         info->gmres_iters += gmres(N, matvec, b.get(), x.get(), 0.1 * tol, gmres_restart, gmres_maxit);
+        {
+          // forcing check: the residual of the projected system with FP64
+          // products; a miss is corrected by GMRES on the FP64 residual
+          const double bnorm = dev_norm(b.get(), N);
+          DBuf<double> r64(N), dx(N);
+          auto true_residual = [&]() {
+            mv_prec = TT_FP64;
+            matvec(x.get(), r64.get());
+            mv_prec = prec;
+            dev_scale(r64.get(), N, -1.0, st);
+            dev_axpy(r64.get(), b.get(), N, 1.0, st);
+            return bnorm > 0 ? dev_norm(r64.get(), N) / bnorm : 0.0;
+          };
+          double rho = true_residual();
+          for (int c = 0; c < 2 && rho > 0.1 * tol && prec != TT_FP64; ++c) {
+            dev_fill(dx.get(), N, 0.0, st);
+            const double rel = std::min(0.5, 0.1 * tol / rho);
+            info->gmres_iters += gmres(N, matvec, r64.get(), dx.get(), rel, gmres_restart, gmres_maxit);
+            dev_axpy(x.get(), dx.get(), N, 1.0, st);
+            ++info->corrections;
+            rho = true_residual();
+          }
+          info->forcing = std::max(info->forcing, rho);
+        }
         dev_copy(nw->get(), x.get(), N, st);
         double* dZ = nw->get() + (nblk - 1) * n;
         apply_sum(eAT, x.get() + n, dZ, 1.0, false);
@@ -420,7 +549,12 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
                         K.get() + rc0 * N + 2 * n, N, 0, 1, st);
         dev_copy2d(b.get() + n, 1, r_t.get(), 1, n, 1, -1.0, st);
       }
-      lu_solve_prec(prec, (int)N, K.get(), b.get());
+      {
+        int corr = 0;
+        const double rho = lu_solve_prec(prec, (int)N, K.get(), b.get(), kLuRefineTol, &corr);
+        info->forcing = std::max(info->forcing, rho);
+        info->corrections += corr;
+      }
       // assemble the new block core [dX, dY, (dT), dZ]
       dev_copy(nw->get(), b.get(), nb * n, st);
       double* dZ = nw->get() + (nblk - 1) * n;
@@ -545,12 +679,29 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         for_all([&](Env& e) { e.push_right(frame, k, prec); });
       }
     }
-    if (sweep >= 1 && max_change < tol) {
-      ++sweep;
-      break;
+    if (prec_in == TT_FP64) {
+      if (sweep >= 1 && max_change < tol) {
+        ++sweep;
+        break;
+      }
+    } else if (prec != TT_FP64) {
+      if ((sweep >= 1 && max_change < std::max(tol, sweep_floor(prec_in))) || sweep + 1 >= max_sweeps) {
+        // switch to FP64: rebuild the environments the next sweep reads
+        prec = TT_FP64;
+        if (forward) {
+          for (int k = 0; k + 1 < d; ++k) for_all([&](Env& e) { e.push_left(frame, k, prec); });
+        } else {
+          for (int k = d - 1; k >= 1; --k) for_all([&](Env& e) { e.push_right(frame, k, prec); });
+        }
+      }
+    } else {
+      ++refine;
+      if (max_change < tol || refine >= kRefineSweeps) {
+        ++sweep;
+        break;
+      }
     }
   }
-  if (sweep > max_sweeps) sweep = max_sweeps;
   info->sweeps = sweep;
   info->max_change = max_change;
   // bring the block index back to core 0 without truncation
@@ -617,7 +768,15 @@ static double local_min_eig(int nl, const double* Mk, const double* Dk, double* 
   dev_axpy(Ds.get(), tmp.get(), nn, 1.0, st);
   dev_scale(Ds.get(), nn, 0.5, st);
   dev_copy(L.get(), Ms.get(), nn, st);
-  cholesky_lower<double>(nl, L.get(), st);
+  DBuf<int> nonpos(1);
+  TT_CUDA(cudaMemsetAsync(nonpos.get(), 0, sizeof(int), st));
+  cholesky_lower<double>(nl, L.get(), st, nonpos.get());
+  int h_nonpos = 0;
+  TT_CUDA(cudaMemcpyAsync(&h_nonpos, nonpos.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaStreamSynchronize(st));
+  // Section 3.4: an iterate that is not positive definite shows in its
+  // projection; the step length is then undefined and the error is raised
+  TT_CHECK(!h_nonpos, TT_E_NOT_PD, "step length: the projected iterate is not positive definite");
   tri_lower_inverse<double>(nl, L.get(), st);  // L <- L^{-1}
   // S = Li Ds Li^T
   gemm_rm<double>(false, false, nl, nl, nl, 1.0, L.get(), nl, 0, Ds.get(), nl, 0, 0.0, tmp.get(), nl, 0, 1, st);
@@ -764,6 +923,134 @@ double min_gen_eig(const DTT& M, const DTT& dM, DTT* e_io, bool warm, Counter& r
   return lam;
 }
 
+// Smallest rank whose discarded tail energy is at most tol^2 of the total, in [1, cap].
+static int dmrg_keep(const std::vector<double>& s, double tol, int cap) {
+  double tot = 0.0;
+  for (double v : s) tot += v * v;
+  int keep = (int)s.size();
+  double tail = 0.0;
+  while (keep > 1 && tail + s[keep - 1] * s[keep - 1] <= tol * tol * tot) {
+    tail += s[keep - 1] * s[keep - 1];
+    --keep;
+  }
+  return std::max(1, std::min(keep, cap));
+}
+
+// Two-site (DMRG) sweeps for min over e of <e, dM e> / <e, M e> (Section 3.4):
+// at bond (k, k+1) the supercore of cores k and k+1 is the local unknown of
+// the projected generalised eigenproblem built from the merged operator
+// cores; the supercore is split by a truncated SVD (relative tolerance tol,
+// at most `rank`), the orthonormal factor is enriched with random columns up
+// to `rank` (kick) and re-orthonormalised by QR, and the other factor is the
+// projection of the supercore onto it.
+double min_gen_eig_dmrg(const DTT& M, const DTT& dM, DTT* e_io, bool warm, Counter& rnd, int rank, int sweeps,
+                        int prec, double tol) {
+  const int d = M.d, nmode = M.m;
+  if (d < 2) return min_gen_eig(M, dM, e_io, warm, rnd, rank, sweeps, prec);
+  cudaStream_t st = cur_stream();
+  DTT e;
+  if (!warm) {
+    std::vector<int> r(d + 1, 1);
+    for (int k = 1; k < d; ++k) {
+      long long cap = 1;
+      int ex = std::min(k, d - k);
+      for (int t = 0; t < ex && cap < rank; ++t) cap *= nmode;
+      r[k] = (int)std::min<long long>(rank, cap);
+    }
+    e = tt_alloc(d, r, nmode, 1);
+    for (int k = 0; k < d; ++k) upload(e.core(k), rnd.draw(e.csize(k)));
+  } else {
+    e = tt_copy(*e_io);
+  }
+  e = tt_orth_right(e);
+  Env eM(M, nullptr, d), eD(dM, nullptr, d);
+  for (int k = d - 1; k >= 2; --k) {
+    eM.push_right(e, k, prec);
+    eD.push_right(e, k, prec);
+  }
+  std::vector<std::shared_ptr<DBuf<double>>> Mm(d - 1), Dm(d - 1);
+  for (int k = 0; k + 1 < d; ++k) {
+    Mm[k] = tt_merge_cores(M, k);
+    Dm[k] = tt_merge_cores(dM, k);
+  }
+  const int n2 = nmode * nmode;
+  double lam = std::numeric_limits<double>::infinity();
+  for (int sw = 0; sw < sweeps; ++sw) {
+    const bool forward = sw % 2 == 0;
+    for (int step = 0; step + 1 < d; ++step) {
+      const int k = forward ? step : d - 2 - step;
+      const int rl = e.r[k], rr = e.r[k + 2];
+      const int nl = rl * n2 * rr;
+      DBuf<double> Mk((size_t)nl * nl), Dk((size_t)nl * nl), x(nl);
+      CDims cm{rl, rr, M.r[k], M.r[k + 2], rl, rr, n2, n2};
+      CDims cd{rl, rr, dM.r[k], dM.r[k + 2], rl, rr, n2, n2};
+      local_matrix(cm, eM.L[k].get(), Mm[k]->get(), eM.R[k + 2].get(), Mk.get(), prec, st);
+      local_matrix(cd, eD.L[k].get(), Dm[k]->get(), eD.R[k + 2].get(), Dk.get(), prec, st);
+      {
+        ProfScope ps("eig.local");
+        lam = local_min_eig(nl, Mk.get(), Dk.get(), x.get());
+      }
+      // split the supercore (rl n) x (n rr)
+      const int rows = rl * nmode, cols = nmode * rr;
+      const int kk = std::min(rows, cols);
+      DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
+      svd_thin<double>(MatView<double>{x.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+      const int keep = dmrg_keep(host_copy(S.get(), kk), tol, rank);
+      const int extra = std::max(0, std::min(rank, kk) - keep);
+      const int nk = keep + extra;
+      if (forward) {
+        // left factor: U[:, :keep] with kick columns, orthonormal
+        DBuf<double> left((size_t)rows * nk);
+        dev_copy2d(left.get(), nk, U.get(), kk, rows, keep, 1.0, st);
+        if (extra > 0) {
+          DBuf<double> rr_((size_t)rows * extra);
+          upload(rr_.get(), rnd.draw((size_t)rows * extra));
+          dev_copy2d(left.get() + keep, nk, rr_.get(), extra, rows, extra, 1.0, st);
+          DBuf<double> Q((size_t)rows * nk), R((size_t)nk * nk);
+          qr_thin<double>(MatView<double>{left.get(), rows, nk, nk, 1}, Q.get(), R.get(), st);
+          dev_copy(left.get(), Q.get(), (size_t)rows * nk, st);
+        }
+        auto ck = std::make_shared<DBuf<double>>((size_t)rows * nk);
+        dev_copy(ck->get(), left.get(), (size_t)rows * nk, st);
+        auto ck1 = std::make_shared<DBuf<double>>((size_t)nk * cols);
+        gemm_rm<double>(true, false, nk, cols, rows, 1.0, left.get(), nk, 0, x.get(), cols, 0, 0.0, ck1->get(), cols,
+                        0, 1, st);
+        e.c[k] = ck;
+        e.c[k + 1] = ck1;
+        e.r[k + 1] = nk;
+        eM.push_left(e, k, prec);
+        eD.push_left(e, k, prec);
+      } else {
+        // right factor: Vt[:keep]^T with kick columns, orthonormal columns
+        DBuf<double> right((size_t)cols * nk), vk((size_t)cols * keep);
+        transpose<double>(keep, cols, Vt.get(), vk.get(), st);
+        dev_copy2d(right.get(), nk, vk.get(), keep, cols, keep, 1.0, st);
+        if (extra > 0) {
+          DBuf<double> rr_((size_t)cols * extra);
+          upload(rr_.get(), rnd.draw((size_t)cols * extra));
+          dev_copy2d(right.get() + keep, nk, rr_.get(), extra, cols, extra, 1.0, st);
+          DBuf<double> Q((size_t)cols * nk), R((size_t)nk * nk);
+          qr_thin<double>(MatView<double>{right.get(), cols, nk, nk, 1}, Q.get(), R.get(), st);
+          dev_copy(right.get(), Q.get(), (size_t)cols * nk, st);
+        }
+        auto ck1 = std::make_shared<DBuf<double>>((size_t)nk * cols);
+        transpose<double>(cols, nk, right.get(), ck1->get(), st);
+        auto ck = std::make_shared<DBuf<double>>((size_t)rows * nk);
+        gemm_rm<double>(false, false, rows, nk, cols, 1.0, x.get(), cols, 0, right.get(), nk, 0, 0.0, ck->get(), nk,
+                        0, 1, st);
+        e.c[k] = ck;
+        e.c[k + 1] = ck1;
+        e.r[k + 1] = nk;
+        eM.push_right(e, k + 1, prec);
+        eD.push_right(e, k + 1, prec);
+      }
+    }
+  }
+  if (e_io) *e_io = tt_orth_right(e);
+  return lam;
+}
+
+
 static double step_from_lambda(double lam) {
   return lam >= 0 ? std::numeric_limits<double>::infinity() : -1.0 / lam;
 }
@@ -838,6 +1125,21 @@ Problem build_cc(const DTT& cp, const DTT& cm, const DTT& a) {
 // ---------------------------------------------------------------------------
 // the interior-point iteration (Algorithm 1 with the choices of Section 3.5)
 // ---------------------------------------------------------------------------
+// The step-length eigensolver the options select: two-site DMRG (Section 3.4)
+// or one-site ALS, FP64 throughout.
+static double gen_eig(const Options& o, const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank,
+                      int sweeps) {
+  if (o.eig_two_site) return min_gen_eig_dmrg(M, dM, e, warm, rnd, rank, sweeps, TT_FP64, kDmrgTol);
+  return min_gen_eig(M, dM, e, warm, rnd, rank, sweeps, TT_FP64);
+}
+
+Solver::~Solver() {
+  for (cudaStream_t s : side_) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+}
+
 Solver::Solver(Problem p, const Options& o) : p_(std::move(p)), o_(o) {
   rnd_.seed = o.seed;
   rnd_.n = 0;
@@ -848,7 +1150,7 @@ Solver::Solver(Problem p, const Options& o) : p_(std::move(p)), o_(o) {
   Y_ = tt_zeros_like_modes(d, 2, 2);
   if (p_.ineq) {
     DTT e;
-    double lmin = min_gen_eig(I_, p_.ones_t, &e, false, rnd_, 2, 6, TT_FP64);
+    double lmin = gen_eig(o_, I_, p_.ones_t, &e, false, rnd_, 2, 6);
     double alpha_p = lmin < 0 ? p_.lam0 * step_from_lambda(lmin) : p_.lam0;
     X_ = tt_add(tt_scale(I_, p_.lam0), p_.ones_t, 1.0, alpha_p / 10.0);
     T_ = tt_scale(p_.ones_t, p_.lam0_ineq);
@@ -931,8 +1233,11 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
   BlockTT w = amen_solve(nd, d, w_ ? w_.get() : nullptr, eta_, o_.rank_cap, o_.kick, o_.max_sweeps, rnd_,
                          o_.prec, o_.local_dense_max, o_.gmres_restart, o_.gmres_max_iters, &info);
   gmres_iters_ += info.gmres_iters;
+  forcing_it_ = std::max(forcing_it_, info.forcing);
+  corrections_ += info.corrections;
   w_ = std::make_unique<BlockTT>(w);
   *sweeps = info.sweeps;
+  amen_ok_ = info.max_change < eta_;
   dX = unvec(w.component(0));
   dY = unvec(w.component(1));
   if (p_.ineq) {
@@ -951,7 +1256,7 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
 
 double Solver::max_step(const DTT& M, const DTT& dM, DTT* e) {
   bool warm = (e == &eX_) ? haveX_ : haveZ_;
-  double lam = min_gen_eig(M, tt_sym(dM), e, warm, rnd_, o_.eig_rank, o_.eig_sweeps, TT_FP64);
+  double lam = gen_eig(o_, M, tt_sym(dM), e, warm, rnd_, o_.eig_rank, o_.eig_sweeps);
   if (e == &eX_) haveX_ = true; else haveZ_ = true;
   return step_from_lambda(lam);
 }
@@ -960,7 +1265,7 @@ double Solver::max_step_diag(const DTT& v, const DTT& dv, DTT* e) {
   DTT idle = tt_add(vecv(tt_ones_mat(p_.d, 2)), vecv(p_.ones_t), 1.0, -1.0);
   DTT M = tt_diag(tt_add(v, idle, 1.0, 1.0));
   bool warm = (e == &eS_) ? haveS_ : haveT_;
-  double lam = min_gen_eig(M, tt_diag(dv), e, warm, rnd_, 1, o_.eig_sweeps, TT_FP64);
+  double lam = gen_eig(o_, M, tt_diag(dv), e, warm, rnd_, 1, o_.eig_sweeps);
   if (e == &eS_) haveS_ = true; else haveT_ = true;
   return step_from_lambda(lam);
 }
@@ -996,8 +1301,8 @@ DTT Solver::round_psd(const DTT& Mx, double delta, const DTT* shift, int var_id)
     hook.trace_y = &trace_y_;
   }
   auto rz = tt_round(vecv(Mx), delta / (1.0 + sn), o_.rank_cap, &hook);
-  pred_used_ += hook.used;
-  pred_fallbacks_ += hook.fallbacks;
+  if (hook.used) pred_used_ += hook.used;
+  if (hook.fallbacks) pred_fallbacks_ += hook.fallbacks;
   DTT rounded = unvec(rz.first);
   double zeta = rz.second;
   if (shift && zeta > 0) rounded = tt_add(rounded, *shift, 1.0, zeta);
@@ -1005,14 +1310,105 @@ DTT Solver::round_psd(const DTT& Mx, double delta, const DTT* shift, int var_id)
   return rounded;
 }
 
+bool Solver::mehrotra(int dir, double mu, bool zp, bool zd, DTT& dX, DTT& dY, DTT& dT, DTT& dZ, double* ap,
+                      double* ad, int* sw) {
+  DTT dXa, dYa, dTa, dZa;
+  direction(dir, 0.0, nullptr, nullptr, nullptr, nullptr, zp, zd, dXa, dYa, dTa, dZa, sw);
+  bool ok = amen_ok_;
+  double apa, ada;
+  {
+    ProfScope ps("ipm.steps");
+    steps(dXa, dTa, dZa, &apa, &ada);
+  }
+  DTT Xa = tt_add(X_, dXa, 1.0, apa), Za = tt_add(Z_, dZa, 1.0, ada);
+  double mu_aff = tt_inner(vecv(Za), vecv(Xa));
+  DTT dsa;
+  if (p_.ineq) {
+    DTT Ta = tt_add(T_, dTa, 1.0, ada);
+    mu_aff += tt_inner(vecv(Ta), slack(Xa));
+    dsa = tt_matvec(p_.A_ineq, vecv(dXa));
+  }
+  mu_aff /= (N_ + p_.q);
+  double ratio = std::min(1.0, std::max(0.0, mu_aff / mu));
+  double sigma = ratio * ratio * ratio;
+  direction(dir, sigma * mu, &dXa, &dZa, p_.ineq ? &dTa : nullptr, p_.ineq ? &dsa : nullptr, zp, zd, dX, dY, dT,
+            dZ, sw);
+  ok = ok && amen_ok_;
+  {
+    ProfScope ps("ipm.steps");
+    steps(dX, dT, dZ, ap, ad);
+  }
+  return ok;
+}
+
+void Solver::apply_update() {
+  ProfScope ps_round("ipm.round");
+  const Update& u = last_;
+  DTT Xn = tt_add(u.X, u.dX, 1.0, u.ap), Zn = tt_add(u.Z, u.dZ, 1.0, u.ad), Yn = tt_add(u.Y, u.dY, 1.0, u.ad), Tn;
+  if (p_.ineq) Tn = tt_add(u.T, u.dT, 1.0, u.ad);
+  DTT Xr, Zr, Yr, Tr;
+  std::vector<std::function<void()>> jobs;
+  jobs.push_back([&]() { Xr = round_psd(Xn, u.tol_p, &I_, 0); });
+  jobs.push_back([&]() { Zr = round_psd(Zn, u.tol_d, &I_, 3); });
+  jobs.push_back([&]() { Yr = round_psd(Yn, u.tol_d, nullptr, 1); });
+  if (p_.ineq) jobs.push_back([&]() { Tr = round_psd(Tn, u.tol_d, &p_.ones_t, 2); });
+  if (pred_ || trace_) {
+    // the predictor's random sketches and the trace share one stream of
+    // draws and one record: keep their order fixed
+    for (auto& j : jobs) j();
+  } else {
+    // the roundings of X, Z, y and t are independent
+    run_concurrently(jobs, side_);
+  }
+  X_ = std::move(Xr);
+  Z_ = std::move(Zr);
+  Y_ = std::move(Yr);
+  if (p_.ineq) T_ = std::move(Tr);
+}
+
 IterLog Solver::iterate() {
+  // an update that the next step-length solve finds outside the cone is
+  // undone and repeated with both step lengths halved (the damp-and-retry
+  // safeguard of Section 3.5), at most kMaxRetries times
+  for (int attempt = 0;; ++attempt) {
+    try {
+      IterLog log = iterate_once();
+      log.retries = retries_;
+      log.fallbacks = fallbacks_;
+      return log;
+    } catch (const TTError& e) {
+      if (e.status != TT_E_NOT_PD || !last_.valid || attempt >= kMaxRetries) throw;
+      last_.ap *= 0.5;
+      last_.ad *= 0.5;
+      apply_update();
+      ++retries_;
+    }
+  }
+}
+
+namespace {
+// CUDA events of one iteration's device time, released on every path
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() {
+    TT_CUDA(cudaEventCreate(&a));
+    TT_CUDA(cudaEventCreate(&b));
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+}  // namespace
+
+IterLog Solver::iterate_once() {
   cudaStream_t st = cur_stream();
-  cudaEvent_t e0, e1;
-  TT_CUDA(cudaEventCreate(&e0));
-  TT_CUDA(cudaEventCreate(&e1));
+  EventPair ev;
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   TT_CUDA(cudaEventRecord(e0, st));
   IterLog log;
   log.iter = it_;
+  forcing_it_ = 0.0;
   Measures ms;
   {
     ProfScope ps("ipm.measures");
@@ -1033,51 +1429,46 @@ IterLog Solver::iterate() {
     log.converged = 1;
   } else {
     eta_ = std::max(std::min(eta_, o_.eta_C * ms.mu), o_.eta_floor);
-    const int dir = it_ < o_.xz_warmup ? 0 : 1;
+    int dir = it_ < o_.xz_warmup ? 0 : 1;
     const bool zp = ms.rel_p <= eps_p, zd = ms.rel_d <= eps_d;
-    DTT dXa, dYa, dTa, dZa;
-    int sw = 0;
-    direction(dir, 0.0, nullptr, nullptr, nullptr, nullptr, zp, zd, dXa, dYa, dTa, dZa, &sw);
-    double apa, ada;
-    {
-      ProfScope ps("ipm.steps");
-      steps(dXa, dTa, dZa, &apa, &ada);
-    }
-    DTT Xa = tt_add(X_, dXa, 1.0, apa), Za = tt_add(Z_, dZa, 1.0, ada);
-    double mu_aff = tt_inner(vecv(Za), vecv(Xa));
-    DTT dsa;
-    if (p_.ineq) {
-      DTT Ta = tt_add(T_, dTa, 1.0, ada);
-      mu_aff += tt_inner(vecv(Ta), slack(Xa));
-      dsa = tt_matvec(p_.A_ineq, vecv(dXa));
-    }
-    mu_aff /= (N_ + p_.q);
-    double ratio = std::min(1.0, std::max(0.0, mu_aff / ms.mu));
-    double sigma = ratio * ratio * ratio;
     DTT dX, dY, dT, dZ;
-    direction(dir, sigma * ms.mu, &dXa, &dZa, p_.ineq ? &dTa : nullptr, p_.ineq ? &dsa : nullptr, zp, zd, dX, dY, dT,
-              dZ, &sw);
-    double ap, ad;
-    {
-      ProfScope ps("ipm.steps");
-      steps(dX, dT, dZ, &ap, &ad);
+    double ap = 0.0, ad = 0.0;
+    int sw = 0;
+    bool ok = mehrotra(dir, ms.mu, zp, zd, dX, dY, dT, dZ, &ap, &ad, &sw);
+    if (dir == 1 && (std::min(ap, ad) < kFallbackStep || !ok)) {
+      // Section 3.5: an AHO solve that misses its target within the rank and
+      // sweep budget, or whose admissible step is nearly zero, is redone with
+      // the XZ direction for this iteration
+      dir = 0;
+      ++fallbacks_;
+      mehrotra(dir, ms.mu, zp, zd, dX, dY, dT, dZ, &ap, &ad, &sw);
     }
     log.alpha_p = ap;
     log.alpha_d = ad;
     log.direction = dir;
     log.sweeps = sw;
     log.max_rank_W = w_->frame.maxrank();
-    const double tol_p = eta_ * (1.0 + nB_) / 10.0, tol_d = eta_ * (1.0 + nC_) / 10.0;
-    ProfScope ps_round("ipm.round");
-    X_ = round_psd(tt_add(X_, dX, 1.0, ap), tol_p, &I_, 0);
-    Z_ = round_psd(tt_add(Z_, dZ, 1.0, ad), tol_d, &I_, 3);
-    Y_ = round_psd(tt_add(Y_, dY, 1.0, ad), tol_d, nullptr, 1);
-    if (p_.ineq) T_ = round_psd(tt_add(T_, dT, 1.0, ad), tol_d, &p_.ones_t, 2);
+    last_.X = X_;
+    last_.Y = Y_;
+    last_.T = T_;
+    last_.Z = Z_;
+    last_.dX = dX;
+    last_.dY = dY;
+    last_.dT = dT;
+    last_.dZ = dZ;
+    last_.ap = ap;
+    last_.ad = ad;
+    last_.tol_p = eta_ * (1.0 + nB_) / 10.0;
+    last_.tol_d = eta_ * (1.0 + nC_) / 10.0;
+    last_.valid = true;
+    apply_update();
     ++it_;
   }
   log.max_rank_X = X_.maxrank();
   log.max_rank_Z = Z_.maxrank();
   log.gmres_iters = gmres_iters_;
+  log.forcing = forcing_it_;
+  log.forcing_corrections = corrections_;
   log.pred_used = pred_used_;
   log.pred_fallbacks = pred_fallbacks_;
   if ((o_.prec == TT_MIXED_TF32 || o_.prec == TT_MIXED_BF16) && tc_check_error(true))
@@ -1087,8 +1478,6 @@ IterLog Solver::iterate() {
   float msec = 0.f;
   TT_CUDA(cudaEventElapsedTime(&msec, e0, e1));
   log.seconds = msec * 1e-3;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return log;
 }
 

@@ -39,6 +39,7 @@ struct Options {
   double eta0 = 1e-3, eta_floor = 1e-4, eta_C = 2.0, damping = 0.95;
   int prec = 0;
   int max_iters = 60, max_sweeps = 4, kick = 4, eig_rank = 4, eig_sweeps = 4;
+  int eig_two_site = 1;  // step lengths by two-site DMRG sweeps; 0: one-site ALS
   uint64_t seed = 1234;
   int local_dense_max = 4096, gmres_restart = 40, gmres_max_iters = 400;
 };
@@ -50,6 +51,10 @@ struct IterLog {
   double seconds = 0;
   long long gmres_iters = 0;
   long long pred_used = 0, pred_fallbacks = 0;
+  double forcing = 0;               // largest FP64 relative residual of a local solve this iteration
+  long long forcing_corrections = 0;
+  long long retries = 0;            // damped retries of updates that left the cone, so far
+  long long fallbacks = 0;          // AHO iterations redone with the XZ direction, so far
 };
 
 class RankPredictor;
@@ -57,6 +62,9 @@ class RankPredictor;
 class Solver {
  public:
   Solver(Problem p, const Options& o);
+  ~Solver();
+  Solver(const Solver&) = delete;
+  Solver& operator=(const Solver&) = delete;
   IterLog iterate();        // one iteration of Algorithm 1
   const DTT& X() const { return X_; }
   const DTT& Y() const { return Y_; }
@@ -85,6 +93,25 @@ class Solver {
   double max_step(const DTT& M, const DTT& dM, DTT* e);
   double max_step_diag(const DTT& v, const DTT& dv, DTT* e);
   DTT round_psd(const DTT& M, double delta, const DTT* shift, int var_id);
+  IterLog iterate_once();
+  // Mehrotra predictor and corrector solves with their step lengths; returns
+  // whether both AMEn solves met their tolerance
+  bool mehrotra(int dir, double mu, bool zp, bool zd, DTT& dX, DTT& dY, DTT& dT, DTT& dZ, double* ap, double* ad,
+                int* sw);
+  static constexpr double kFallbackStep = 1e-3;
+  bool amen_ok_ = true;
+  long long fallbacks_ = 0;
+  void apply_update();  // X, Y, T, Z <- rounded (last_ iterate + step lengths x direction)
+
+  // the last update of Algorithm 1, kept so that it can be damped and redone
+  struct Update {
+    DTT X, Y, T, Z, dX, dY, dT, dZ;
+    double ap = 0.0, ad = 0.0, tol_p = 0.0, tol_d = 0.0;
+    bool valid = false;
+  };
+  static constexpr int kMaxRetries = 4;
+  Update last_;
+  long long retries_ = 0;
 
   Problem p_;
   Options o_;
@@ -99,13 +126,20 @@ class Solver {
   std::vector<float> trace_x_, trace_y_;
   std::vector<int> prev_[4];
   long long pred_used_ = 0, pred_fallbacks_ = 0;
+  double forcing_it_ = 0.0;
+  long long corrections_ = 0;
   std::unique_ptr<BlockTT> w_;
   DTT eX_, eZ_, eT_, eS_;
   bool haveX_ = false, haveZ_ = false, haveT_ = false, haveS_ = false;
+  std::vector<cudaStream_t> side_;  // streams of the concurrent roundings
 };
 
-// Exposed for tests through the C ABI: min over e of <e, dM e>/<e, M e>.
+// min over e of <e, dM e>/<e, M e> (M positive definite): one-site ALS and
+// two-site DMRG sweeps (relative SVD truncation tolerance tol at each split).
 double min_gen_eig(const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank, int sweeps,
                    int prec);
+double min_gen_eig_dmrg(const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank, int sweeps,
+                        int prec, double tol);
+constexpr double kDmrgTol = 1e-8;
 
 }  // namespace ttsdp

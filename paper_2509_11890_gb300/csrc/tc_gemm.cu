@@ -306,14 +306,15 @@ void tc_gemm_tn(int prec, int M, int N, int K, int batch, const void* A, long lo
   const int esz = bf16 ? 2 : 4;
   const long long ld = K;  // operands are packed with a padded K (multiple of 8)
   TT_CHECK((ld * esz) % 16 == 0, TT_E_INTERNAL, "tc_gemm_tn: K must be padded to 16 bytes");
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[bf16]) {
-    if (bf16)
-      TT_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<kFmtBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-    else
-      TT_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<kFmtTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-    attr_set[bf16] = true;
-  }
+  static std::once_flag attr_once[2];
+  cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once[bf16], [&]() {
+    attr_err = bf16 ? cudaFuncSetAttribute(tc_gemm_kernel<kFmtBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kSmemBytes)
+                    : cudaFuncSetAttribute(tc_gemm_kernel<kFmtTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kSmemBytes);
+  });
+  TT_CUDA(attr_err);
   dim3 grid((unsigned)((N + TC_BN - 1) / TC_BN), (unsigned)((M + TC_BM - 1) / TC_BM));
   for (int b = 0; b < batch; ++b) {
     const char* pa = (const char*)A + (size_t)b * sA * esz;
@@ -359,11 +360,16 @@ void tc_gemm_f64_tn(int M, int N, int K, const double* A, long long lda, const d
 }
 
 int tc_check_error(bool reset) {
+  // read on the caller's stream, after the work it has queued (contexts solved
+  // concurrently run on non-blocking streams the legacy stream does not order)
+  cudaStream_t st = cur_stream();
   int h = 0;
-  TT_CUDA(cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int)));
+  TT_CUDA(cudaMemcpyFromSymbolAsync(&h, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaStreamSynchronize(st));
   if (reset && h) {
     int z = 0;
-    TT_CUDA(cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int)));
+    TT_CUDA(cudaMemcpyToSymbolAsync(g_tc_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+    TT_CUDA(cudaStreamSynchronize(st));
   }
   return h;
 }

@@ -115,6 +115,27 @@ __global__ void transpose_core_kernel(const double* A, int r, int m, int n, int 
   }
 }
 
+// out[p][(i1 i2)][(j1 j2)][q] = sum_s A[p][i1][j1][s] B[s][i2][j2][q]
+__global__ void merge_cores_kernel(const double* A, int R, int m1, int n1, int S, const double* B, int m2,
+                                   int n2, int R2, double* out) {
+  long long tot = (long long)R * m1 * m2 * n1 * n2 * R2;
+  GRID_LOOP(e, tot) {
+    long long t = e;
+    int q = (int)(t % R2); t /= R2;
+    int j2 = (int)(t % n2); t /= n2;
+    int j1 = (int)(t % n1); t /= n1;
+    int i2 = (int)(t % m2); t /= m2;
+    int i1 = (int)(t % m1); t /= m1;
+    int p = (int)t;
+    const double* a = A + (((long long)p * m1 + i1) * n1 + j1) * S;
+    const double* b = B + ((long long)i2 * n2 + j2) * R2 + q;
+    const long long bs = (long long)m2 * n2 * R2;
+    double acc = 0.0;
+    for (int x = 0; x < S; ++x) acc += a[x] * b[x * bs];
+    out[e] = acc;
+  }
+}
+
 __global__ void diag_core_kernel(const double* v, int r, int m, int r2, double* out) {
   long long tot = (long long)r * m * m * r2;
   GRID_LOOP(e, tot) {
@@ -391,6 +412,19 @@ DTT tt_matvec(const DTT& op, const DTT& v) {
   return t;
 }
 
+std::shared_ptr<DBuf<double>> tt_merge_cores(const DTT& op, int k) {
+  TT_CHECK(k >= 0 && k + 1 < op.d, TT_E_INVALID_ARG, "tt_merge_cores: bond out of range");
+  const int R = op.r[k], S = op.r[k + 1], R2 = op.r[k + 2];
+  const long long tot = (long long)R * op.m * op.m * op.n * op.n * R2;
+  auto out = std::make_shared<DBuf<double>>((size_t)tot);
+  cudaStream_t st = cur_stream();
+  merge_cores_kernel<<<grid1(tot), 256, 0, st>>>(op.core(k), R, op.m, op.n, S, op.core(k + 1), op.m, op.n, R2,
+                                                 out->get());
+  count_launch();
+  check_launch("merge_cores_kernel");
+  return out;
+}
+
 DTT tt_diag(const DTT& v) {
   int M = v.m * v.n;
   DTT t = tt_alloc(v.d, v.r, M, M);
@@ -624,7 +658,12 @@ static int round_bond_sketch(DTT& t, int k, int l, double thr, int cap, Counter&
 std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* hook) {
   const int d = a.d, M = a.m * a.n;
   cudaStream_t st = cur_stream();
-  DTT t = tt_orth_right(a);
+  DTT t;
+  {
+    ProfScope ps("round.orth");
+    t = tt_orth_right(a);
+  }
+  ProfScope ps_trunc("round.trunc");
   const double thr = delta / std::sqrt((double)(d > 1 ? d - 1 : 1));
   double zeta2 = 0.0;
   // features and predicted ranks of all bonds (one MLP evaluation)
@@ -656,7 +695,10 @@ std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* 
     }
     DBuf<double> U((size_t)rows * kk), S((size_t)kk), Vt((size_t)kk * r2);
     MatView<double> v{t.core(k), rows, r2, r2, 1};
-    svd_thin<double>(v, U.get(), S.get(), Vt.get(), st);
+    {
+      ProfScope ps("round.svd");
+      svd_thin<double>(v, U.get(), S.get(), Vt.get(), st);
+    }
     std::vector<double> hs(kk);
     TT_CUDA(cudaMemcpyAsync(hs.data(), S.get(), kk * sizeof(double), cudaMemcpyDeviceToHost, st));
     TT_CUDA(cudaStreamSynchronize(st));

@@ -184,7 +184,8 @@ def theta_hypercube_kron(d: int, seed: int, lo: float = 0.008, hi: float = 0.015
         adj = q | kron_dense(pats).astype(bool)
         np.fill_diagonal(adj, False)
         dens = adj.sum() / (n * (n - 1))
-        if lo <= dens <= hi or d < 6:
+        # below d = 10 the cube alone is denser than the window: take the first draw
+        if lo <= dens <= hi or d < 6 or d / (n - 1) > hi:
             break
         g_stream += 1
     return {

@@ -102,3 +102,31 @@ def test_tt_from_dense_matches_oracle_tt_svd():
     np.testing.assert_allclose(tt.full_mat(cores), w, atol=1e-10)
     ref = tp.graph_tt(w, eps_rel=1e-13)
     assert tt.ranks(cores) == tt.ranks(ref)
+
+
+def test_concurrent_batch_matches_single_solves():
+    insts = [inputs.maxcut_kron(d, 10 + d) for d in (3, 4, 5, 3, 4, 5)]
+    ctxs = [tg.Context.maxcut(i["adjacency_cores"], _opts()) for i in insts]
+    res = tg.solve_batch(ctxs, workers=3)
+    for inst, r in zip(insts, res):
+        ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]))
+        assert r["status"] == 0, r
+        assert abs(r["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3
+        assert r["seconds"] > 0
+
+
+@pytest.mark.parametrize("prec,dense_max", [(tg.FP64, 4096), (tg.MIXED_TF32, 4096), (tg.MIXED_TF32, 0)])
+def test_forcing_check_reports_fp64_local_residuals(prec, dense_max):
+    # row a11: every local solve's FP64 residual against the projected
+    # operator is measured; the forcing condition ||E|| <= eta ||R|| holds
+    # with eta <= eta0 = 1e-3 (LU refined to 1e-10, GMRES to eta/10)
+    inst = inputs.maxcut_kron(4, 2)
+    ctx = tg.Context.maxcut(inst["adjacency_cores"], _opts(precision=prec, local_dense_max=dense_max))
+    for _ in range(4):
+        info = ctx.newton_step()
+        if info["converged"]:
+            break
+        assert 0.0 < info["forcing"] < 1e-3, info
+        if dense_max > 0:
+            assert info["forcing"] <= 1e-6, info
+    assert info["forcing_corrections"] >= 0

@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import scipy.linalg
 import pytest
 
 from oracle import sdp_dense as sd, tt, tt_ipm, tt_problems as tp
@@ -125,3 +126,102 @@ def test_ipm_cc_reaches_dense_optimum():
     h = ipm.history[-1]
     assert ok, h
     assert abs(h.pobj - ref.pobj) / (1 + abs(ref.pobj)) <= 5e-3
+
+
+def _pd_pair(d, seed, rank=2):
+    g = inputs.random_tt_matrix([2] * d, [2] * d, [1] + [rank] * (d - 1) + [1], seed + 40)
+    gs = tt.add(g, tt.transpose(g), 0.5, 0.5)
+    shift = abs(np.linalg.eigvalsh(tt.full_mat(gs))[0]) + 1.0
+    M = tt.add(tt.scale(tt.identity(d), shift), gs)
+    h = inputs.random_tt_matrix([2] * d, [2] * d, [1] + [rank] * (d - 1) + [1], seed + 50)
+    dM = tt.add(h, tt.transpose(h), 0.5, 0.5)
+    return M, dM
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_merged_operator_cores_define_the_same_matrix(k):
+    d = 4
+    M, _ = _pd_pair(d, 3)
+    merged = M[:k] + [tt_ipm.merge_op_cores(M, k)] + M[k + 2:]
+    np.testing.assert_allclose(tt.full_mat(merged), tt.full_mat(M), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_dmrg_step_length_matches_dense_rule(seed):
+    # rank 4 is full rank at every bond of d = 4: the two-site quotient is exact
+    d = 4
+    M, dM = _pd_pair(d, seed)
+    ref = sd.max_step(tt.full_mat(M), tt.full_mat(dM))
+    lam, e = tt_ipm.min_gen_eig_dmrg(M, dM, None, tt_ipm.Counter(seed), rank=4, sweeps=4)
+    assert math.isclose(tt_ipm.step_from_lambda(lam), ref, rel_tol=1e-8)
+    # the returned vector attains the returned quotient
+    ev = tt.full_vec(e)
+    Md, dMd = tt.full_mat(M), tt.full_mat(dM)
+    assert math.isclose(ev @ dMd @ ev / (ev @ Md @ ev), lam, rel_tol=1e-8, abs_tol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [2, 3, 4])
+def test_dmrg_finds_rank_one_extreme_eigenvector(seed):
+    # M = I, dM = diag(v): the minimum quotient is min(v), attained at a unit
+    # vector (TT rank one), found by two-site sweeps with rank 2
+    d = 6
+    v = inputs.random_tt([2] * d, [1] + [2] * (d - 1) + [1], seed)
+    M = tt.identity(d)
+    dM = tt.diag_tt(v)
+    lam, e = tt_ipm.min_gen_eig_dmrg(M, dM, None, tt_ipm.Counter(seed), rank=2, sweeps=6)
+    vmin = float(np.min(tt.full_vec(v)))
+    assert math.isclose(lam, vmin, rel_tol=1e-8, abs_tol=1e-10)
+
+
+def test_dmrg_quotient_bounds_the_dense_minimum_from_above():
+    d = 6
+    M, dM = _pd_pair(d, 7, rank=3)
+    dense = float(scipy.linalg.eigh(tt.full_mat(dM), tt.full_mat(M), eigvals_only=True)[0])
+    lam, _ = tt_ipm.min_gen_eig_dmrg(M, dM, None, tt_ipm.Counter(7), rank=2, sweeps=4)
+    assert lam >= dense - 1e-10
+    lam8, _ = tt_ipm.min_gen_eig_dmrg(M, dM, None, tt_ipm.Counter(7), rank=8, sweeps=4)
+    assert lam8 >= dense - 1e-10 and lam8 <= lam + 1e-12
+    assert math.isclose(lam8, dense, rel_tol=1e-6)
+
+
+def test_dmrg_keep_rule():
+    s = np.array([1.0, 1e-3, 1e-6, 1e-9])
+    assert tt_ipm.dmrg_keep(s, 1e-8, 10) == 3
+    assert tt_ipm.dmrg_keep(s, 1e-4, 10) == 2
+    assert tt_ipm.dmrg_keep(s, 1e-8, 2) == 2
+    assert tt_ipm.dmrg_keep(np.array([1.0]), 1e-8, 4) == 1
+
+
+@pytest.mark.parametrize("two_site", [True, False])
+def test_indefinite_iterate_raises(two_site):
+    d = 4
+    M, dM = _pd_pair(d, 0)
+    Mneg = tt.add(M, tt.identity(d), 1.0, -100.0)
+    fn = tt_ipm.min_gen_eig_dmrg if two_site else tt_ipm.min_gen_eig
+    with pytest.raises(tt_ipm.NotPositiveDefinite):
+        fn(Mneg, dM, None, tt_ipm.Counter(0), 4, 2)
+
+
+def test_damp_and_retry_repairs_an_update_that_left_the_cone():
+    # plant an overlong step after the first iteration: the next step-length
+    # solve finds X outside the cone, the update is redone with halved steps
+    # until X is positive definite again, and the solve still reaches the optimum
+    d, seed = 4, 2
+    inst, prob = _maxcut(d, seed)
+    ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]))
+    ipm = tt_ipm.TTIPM(prob, tt_ipm.Options(rank_cap=16, max_iters=40))
+    assert ipm.iterate(0) is not None
+    lam0 = np.linalg.eigvalsh(tt.full_mat(ipm.prev["dX"]))[0]
+    assert lam0 < 0
+    # a step three times past the boundary of the cone along dX
+    ipm.prev["ap"] = 3.0 * tt_ipm.step_from_lambda(
+        float(scipy.linalg.eigh(tt.full_mat(ipm.prev["dX"]), tt.full_mat(ipm.prev["X"]), eigvals_only=True)[0]))
+    ipm._apply_update()
+    assert np.linalg.eigvalsh(tt.full_mat(ipm.X))[0] < 0
+    for it in range(1, 41):
+        if ipm.iterate(it) is None:
+            break
+    assert ipm.retries >= 1
+    assert np.linalg.eigvalsh(tt.full_mat(ipm.X))[0] > 0
+    h = ipm.history[-1]
+    assert abs(h.pobj - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3
