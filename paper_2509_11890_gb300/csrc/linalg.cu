@@ -281,19 +281,24 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
 }
 
 // ---------------------------------------------------------------------------
-// blocked LU with partial pivoting on [A | b]
+// Blocked LU with partial pivoting of M = A^T. The row-major buffer of A is
+// the column-major buffer of M (M[i][j] at p[j*n + i]), so every column of M
+// the panel touches is a contiguous row of A: the pivot search, the scaling
+// and the rank-1 updates read consecutive addresses. P M = L U; then
+// A = M^T = U^T L^T P and A x = b is solved by U^T y = b, L^T z = y, x = P^T z.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) lu_panel_kernel(int n, T* A, T* b, int j0, int jb, int* ipiv) {
+__global__ void __launch_bounds__(kThreads) lu_panel_kernel(int n, T* B, int j0, int jb, int* ipiv) {
   __shared__ T rv[kWarps];
   __shared__ int ri[kWarps];
   __shared__ int s_piv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int jj = j0; jj < j0 + jb; ++jj) {
+    T* col = B + (long long)jj * n;  // column jj of M
     T best = T(-1);
     int bi = jj;
     for (int i = jj + tid; i < n; i += kThreads) {
-      T v = fabs(A[(long long)i * n + jj]);
+      T v = fabs(col[i]);
       if (v > best) { best = v; bi = i; }
     }
 #pragma unroll
@@ -315,62 +320,63 @@ __global__ void __launch_bounds__(kThreads) lu_panel_kernel(int n, T* A, T* b, i
     __syncthreads();
     const int piv = s_piv;
     if (piv != jj) {
+      // interchange rows jj and piv of M inside the panel
       for (int c = j0 + tid; c < j0 + jb; c += kThreads) {
-        T t = A[(long long)jj * n + c];
-        A[(long long)jj * n + c] = A[(long long)piv * n + c];
-        A[(long long)piv * n + c] = t;
+        T* cc = B + (long long)c * n;
+        T t = cc[jj];
+        cc[jj] = cc[piv];
+        cc[piv] = t;
       }
     }
     __syncthreads();
-    const T p = A[(long long)jj * n + jj];
+    const T p = col[jj];
     const T inv = p != T(0) ? T(1) / p : T(0);
-    for (int i = jj + 1 + tid; i < n; i += kThreads) A[(long long)i * n + jj] *= inv;
+    for (int i = jj + 1 + tid; i < n; i += kThreads) col[i] *= inv;
     __syncthreads();
-    const int ncol = j0 + jb - (jj + 1);
-    if (ncol > 0) {
-      long long tot = (long long)(n - jj - 1) * ncol;
-      for (long long e = tid; e < tot; e += kThreads) {
-        int i = jj + 1 + (int)(e / ncol), c = jj + 1 + (int)(e % ncol);
-        A[(long long)i * n + c] -= A[(long long)i * n + jj] * A[(long long)jj * n + c];
-      }
+    // rank-1 update of the panel's remaining columns, one warp per column
+    for (int c = jj + 1 + warp; c < j0 + jb; c += kWarps) {
+      T* cc = B + (long long)c * n;
+      const T u = cc[jj];
+      if (u != T(0))
+        for (int i = jj + 1 + lane; i < n; i += 32) cc[i] -= col[i] * u;
     }
     __syncthreads();
   }
 }
 
+// Row interchanges of the panel and the unit-lower triangular solve with its
+// L11 for every column of M outside the panel, one thread per column.
 template <typename T>
-__global__ void lu_swap_trsm_kernel(int n, T* A, T* b, int j0, int jb, const int* ipiv) {
-  // one thread per column outside the panel (and the right-hand side, if any)
+__global__ void lu_swap_trsm_kernel(int n, T* B, int j0, int jb, const int* ipiv) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int ncols = n - jb + (b ? 1 : 0);
-  if (c >= ncols) return;
-  int col = c < j0 ? c : c + jb;  // skip the panel columns; col == n means b
-  auto at = [&](int i) -> T& { return col < n ? A[(long long)i * n + col] : b[i]; };
+  if (c >= n - jb) return;
+  const int col = c < j0 ? c : c + jb;  // skip the panel columns
+  T* cc = B + (long long)col * n;
   for (int jj = j0; jj < j0 + jb; ++jj) {
-    int piv = ipiv[jj];
+    const int piv = ipiv[jj];
     if (piv != jj) {
-      T t = at(jj);
-      at(jj) = at(piv);
-      at(piv) = t;
+      T t = cc[jj];
+      cc[jj] = cc[piv];
+      cc[piv] = t;
     }
   }
   if (col >= j0 + jb) {
-    // unit lower triangular solve with the panel's L11
     for (int r = 1; r < jb; ++r) {
-      T s = at(j0 + r);
-      for (int t = 0; t < r; ++t) s -= A[(long long)(j0 + r) * n + j0 + t] * at(j0 + t);
-      at(j0 + r) = s;
+      T s = cc[j0 + r];
+      for (int t = 0; t < r; ++t) s -= B[(long long)(j0 + t) * n + j0 + r] * cc[j0 + t];
+      cc[j0 + r] = s;
     }
   }
 }
 
-// Forward and backward substitution with the factors of lu_factor for one
-// right-hand side: the row interchanges, then unit-lower and upper solves in
-// blocks of 32 rows (the off-block part of each row is a warp dot product
-// over a contiguous row segment, the 32 x 32 triangle runs in one warp).
-// x lives in shared memory when it fits, else in b itself.
+// Solves A x = b with the factors of M = A^T (P M = L U in the buffer):
+// U^T y = b (lower, row i of U^T = column i of U, contiguous), L^T z = y
+// (upper with unit diagonal, row i of L^T = column i of L), x = P^T z. Both
+// triangular solves go in blocks of 32 rows: the off-block part of a row is a
+// warp dot product, the 32 x 32 triangle runs in one warp. x lives in shared
+// memory when it fits, else in b itself.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* A, const int* ipiv, T* b,
+__global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* B, const int* ipiv, T* b,
                                                             bool use_smem) {
   extern __shared__ __align__(16) unsigned char lu_smem[];
   T* x = use_smem ? reinterpret_cast<T*>(lu_smem) : b;
@@ -378,20 +384,11 @@ __global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* A, c
   if (use_smem)
     for (int i = tid; i < n; i += kThreads) x[i] = b[i];
   __syncthreads();
-  if (tid == 0)
-    for (int j = 0; j < n; ++j) {
-      const int p = ipiv[j];
-      if (p != j) {
-        T t = x[j];
-        x[j] = x[p];
-        x[p] = t;
-      }
-    }
-  __syncthreads();
+  // U^T y = b
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int ib = n - i0 < 32 ? n - i0 : 32;
     for (int r = warp; r < ib; r += kWarps) {
-      const T* row = A + (long long)(i0 + r) * n;
+      const T* row = B + (long long)(i0 + r) * n;
       T s = T(0);
       for (int t = lane; t < i0; t += 32) s += row[t] * x[t];
       s = warp_sum(s);
@@ -399,30 +396,9 @@ __global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* A, c
     }
     __syncthreads();
     if (warp == 0) {
-      for (int r = 1; r < ib; ++r) {
-        const T* row = A + (long long)(i0 + r) * n + i0;
+      for (int r = 0; r < ib; ++r) {
+        const T* row = B + (long long)(i0 + r) * n + i0;
         T s = lane < r ? row[lane] * x[i0 + lane] : T(0);
-        s = warp_sum(s);
-        if (lane == 0) x[i0 + r] -= s;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-  }
-  for (int i1 = n; i1 > 0; i1 -= 32) {
-    const int i0 = i1 - 32 > 0 ? i1 - 32 : 0, ib = i1 - i0;
-    for (int r = warp; r < ib; r += kWarps) {
-      const T* row = A + (long long)(i0 + r) * n;
-      T s = T(0);
-      for (int t = i1 + lane; t < n; t += 32) s += row[t] * x[t];
-      s = warp_sum(s);
-      if (lane == 0) x[i0 + r] -= s;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      for (int r = ib - 1; r >= 0; --r) {
-        const T* row = A + (long long)(i0 + r) * n + i0;
-        T s = (lane > r && lane < ib) ? row[lane] * x[i0 + lane] : T(0);
         s = warp_sum(s);
         if (lane == 0) {
           const T dg = row[r];
@@ -433,6 +409,39 @@ __global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* A, c
     }
     __syncthreads();
   }
+  // L^T z = y
+  for (int i1 = n; i1 > 0; i1 -= 32) {
+    const int i0 = i1 - 32 > 0 ? i1 - 32 : 0, ib = i1 - i0;
+    for (int r = warp; r < ib; r += kWarps) {
+      const T* row = B + (long long)(i0 + r) * n;
+      T s = T(0);
+      for (int t = i1 + lane; t < n; t += 32) s += row[t] * x[t];
+      s = warp_sum(s);
+      if (lane == 0) x[i0 + r] -= s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int r = ib - 1; r >= 0; --r) {
+        const T* row = B + (long long)(i0 + r) * n + i0;
+        T s = (lane > r && lane < ib) ? row[lane] * x[i0 + lane] : T(0);
+        s = warp_sum(s);
+        if (lane == 0) x[i0 + r] -= s;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  // x = P^T z: the interchanges in reverse order
+  if (tid == 0)
+    for (int j = n - 1; j >= 0; --j) {
+      const int p = ipiv[j];
+      if (p != j) {
+        T t = x[j];
+        x[j] = x[p];
+        x[p] = t;
+      }
+    }
+  __syncthreads();
   if (use_smem)
     for (int i = tid; i < n; i += kThreads) b[i] = x[i];
 }
@@ -551,14 +560,16 @@ void lu_factor(int n, T* A, int* ipiv, cudaStream_t st) {
   constexpr int nb = 32;
   for (int j0 = 0; j0 < n; j0 += nb) {
     int jb = n - j0 < nb ? n - j0 : nb;
-    lu_panel_kernel<T><<<1, kThreads, 0, st>>>(n, A, nullptr, j0, jb, ipiv);
+    lu_panel_kernel<T><<<1, kThreads, 0, st>>>(n, A, j0, jb, ipiv);
     count_launch();
     int ncols = n - jb;
     if (ncols > 0) {
-      lu_swap_trsm_kernel<T><<<ceil_div(ncols, 128), 128, 0, st>>>(n, A, nullptr, j0, jb, ipiv);
+      lu_swap_trsm_kernel<T><<<ceil_div(ncols, 128), 128, 0, st>>>(n, A, j0, jb, ipiv);
       count_launch();
     }
     int rest = n - j0 - jb;
+    // M22 -= M21 M12 in M's column-major layout is, on the row-major views of
+    // the same buffer, M22^T -= M12^T M21^T
     if (rest > 0)
       gemm_rm<T>(false, false, rest, rest, jb, T(-1), A + (long long)(j0 + jb) * n + j0, n, 0,
                  A + (long long)j0 * n + j0 + jb, n, 0, T(1), A + (long long)(j0 + jb) * n + j0 + jb, n,

@@ -30,10 +30,11 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st);
 template <typename T>
 void lu_solve(int n, T* A, T* b, cudaStream_t st);
 
-// The two halves of lu_solve: lu_factor overwrites A with its unit-lower L
-// and upper U factors (P A = L U, row interchanges in ipiv, n entries);
-// lu_solve_factored then solves A x = b in place for one right-hand side
-// and may be called any number of times on the same factors.
+// The two halves of lu_solve: lu_factor overwrites the row-major A with the
+// factors of its transpose (P A^T = L U with partial pivoting, stored
+// column-major: the buffer read row-major holds L^T and U^T; interchanges in
+// ipiv, n entries); lu_solve_factored then solves A x = b in place for one
+// right-hand side and may be called any number of times on the same factors.
 template <typename T>
 void lu_factor(int n, T* A, int* ipiv, cudaStream_t st);
 template <typename T>

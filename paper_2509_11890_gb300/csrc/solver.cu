@@ -784,20 +784,27 @@ static double local_min_eig(int nl, const double* Mk, const double* Dk, double* 
   transpose<double>(nl, nl, S.get(), tmp.get(), st);
   dev_axpy(S.get(), tmp.get(), nn, 1.0, st);
   dev_scale(S.get(), nn, 0.5, st);
-  // smallest eigenpair of the symmetric S through the SVD of S + s I (s >= ||S||_F)
+  // smallest eigenvector of the symmetric S from an FP32 Jacobi SVD of S + s I
+  // (s >= ||S||_F makes every eigenvalue positive, so the smallest singular
+  // pair is the smallest eigenpair); its eigenvalue is then the FP64 Rayleigh
+  // quotient v^T S v / v^T v, whose error is second order in the FP32 error of v
   double s = dev_norm(S.get(), nn) + 1e-300;
   std::vector<double> diag(nn, 0.0);
   for (int i = 0; i < nl; ++i) diag[(size_t)i * nl + i] = s;
-  DBuf<double> dI(nn);
+  DBuf<double> Sh(nn), dI(nn);
   upload(dI.get(), diag);
-  dev_axpy(S.get(), dI.get(), nn, 1.0, st);
-  DBuf<double> U(nn), Sv(nl), Vt(nn);
-  svd_thin<double>(MatView<double>{S.get(), nl, nl, nl, 1}, U.get(), Sv.get(), Vt.get(), st);
-  std::vector<double> hs = host_copy(Sv.get(), nl);
-  double lam = hs[nl - 1] - s;
-  // v = last column of U; x = Li^T v
-  DBuf<double> v(nl);
-  dev_copy2d(v.get(), 1, U.get() + (nl - 1), nl, nl, 1, 1.0, st);
+  dev_copy(Sh.get(), S.get(), nn, st);
+  dev_axpy(Sh.get(), dI.get(), nn, 1.0, st);
+  DBuf<float> Sf(nn), U(nn), Sv(nl), Vt(nn);
+  to_f32(Sh.get(), Sf.get(), nn, st);
+  svd_thin<float>(MatView<float>{Sf.get(), nl, nl, nl, 1}, U.get(), Sv.get(), Vt.get(), st);
+  DBuf<double> v(nl), Sv64(nl);
+  transpose<float>(nl, nl, U.get(), Vt.get(), st);  // row nl-1 of U^T = last column of U
+  to_f64(Vt.get() + (size_t)(nl - 1) * nl, v.get(), nl, st);
+  gemm_rm<double>(false, false, nl, 1, nl, 1.0, S.get(), nl, 0, v.get(), 1, 0, 0.0, Sv64.get(), 1, 0, 1, st);
+  const double num = dev_dot(v.get(), Sv64.get(), nl, st), den = dev_dot(v.get(), v.get(), nl, st);
+  const double lam = den > 0 ? num / den : 0.0;
+  // x = Li^T v
   gemm_rm<double>(true, false, nl, 1, nl, 1.0, L.get(), nl, 0, v.get(), 1, 0, 0.0, x, 1, 0, 1, st);
   return lam;
 }
