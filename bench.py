@@ -43,7 +43,7 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=12)
+    p.add_argument("--steps", type=int, default=6)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="maxcut_d10_kron_er_cap64", choices=sorted(WORKLOADS))

@@ -7,6 +7,7 @@
 // strided GEMM.
 #include <cfloat>
 #include <mutex>
+#include <type_traits>
 
 #include "gemm.cuh"
 #include "linalg.cuh"
@@ -146,7 +147,8 @@ __global__ void __launch_bounds__(kThreads) qr_kernel(MatView<T> A, T* W, T* tau
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transposed, T* Wg, T* Vg, bool w_smem,
-                                                       bool v_smem, T* U, T* S, T* Vt, int* perm) {
+                                                       bool v_smem, T* U, T* S, T* Vt, int* perm, const T* V0,
+                                                       bool need_v) {
   __shared__ int s_rot;
   // the working columns live in shared memory when they fit (every rotation
   // then costs shared-memory latency instead of an L2 round trip)
@@ -161,10 +163,13 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
     int j = (int)(idx / m), i = (int)(idx % m);  // column j, row i of B
     Wc[idx] = transposed ? A.p[j * A.rs + i * A.cs] : A.p[i * A.rs + j * A.cs];
   }
-  for (long long idx = tid; idx < (long long)n * n; idx += kThreads) {
-    int j = (int)(idx / n), i = (int)(idx % n);
-    Vc[idx] = i == j ? T(1) : T(0);
-  }
+  // accumulated right rotations start from V0 (row-major n x n) when given:
+  // B = W V0^T with W = A on entry, so the sweeps only have to finish the job
+  if (need_v)
+    for (long long idx = tid; idx < (long long)n * n; idx += kThreads) {
+      int j = (int)(idx / n), i = (int)(idx % n);
+      Vc[idx] = V0 ? V0[(long long)i * n + j] : (i == j ? T(1) : T(0));
+    }
   __syncthreads();
   // rotation threshold: a length-m dot product carries about sqrt(m) eps of
   // rounding noise, so a smaller threshold never lets the sweeps terminate
@@ -217,12 +222,14 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
             wp[i] = c * u - s * v;
             wq[i] = s * u + c * v;
           }
-          T* vp = Vc + (long long)p * n;
-          T* vq = Vc + (long long)q * n;
-          for (int i = lane; i < n; i += 32) {
-            T u = vp[i], v = vq[i];
-            vp[i] = c * u - s * v;
-            vq[i] = s * u + c * v;
+          if (need_v) {
+            T* vp = Vc + (long long)p * n;
+            T* vq = Vc + (long long)q * n;
+            for (int i = lane; i < n; i += 32) {
+              T u = vp[i], v = vq[i];
+              vp[i] = c * u - s * v;
+              vq[i] = s * u + c * v;
+            }
           }
           if (lane == 0) s_rot = 1;
         }
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
     if (!transposed) U[(long long)i * k + r] = val;       // U (m x k)
     else Vt[(long long)r * m + i] = val;                   // Vt (k x m)
   }
-  for (long long idx = tid; idx < (long long)n * k; idx += kThreads) {
+  for (long long idx = tid; need_v && idx < (long long)n * k; idx += kThreads) {
     int j = (int)(idx / k), r = (int)(idx % k);
     T val = Vc[(long long)perm[r] * n + j];
     if (!transposed) Vt[(long long)r * n + j] = val;       // Vt (k x n)
@@ -501,6 +508,40 @@ __global__ void transpose_kernel(int m, int n, const T* in, T* out) {
   out[(long long)j * m + i] = in[idx];
 }
 
+// out (rows x cols, row-major) <- the view p with out[i][j] = p[i * s0 + j * s1]
+template <typename T>
+__global__ void transpose_view_kernel(const T* p, long long s1, long long s0, int rows, int cols, T* out) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / cols, j = e % cols;
+    out[e] = p[i * s0 + j * s1];
+  }
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(const S* in, long long n, D* out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = (D)in[e];
+}
+
+// G <- (3 I - G) / 2
+__global__ void newton_schulz_rhs_kernel(double* G, int n) {
+  const long long tot = (long long)n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    G[e] = ((i == j ? 3.0 : 0.0) - G[e]) * 0.5;
+  }
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  return (int)(g > 152 * 16 ? 152 * 16 : g);
+}
+
+// FP64 Jacobi SVDs with at least this many columns get an FP32 preconditioner
+constexpr int kPrecondMinCols = 16;
+
 }  // namespace
 
 template <typename T>
@@ -514,7 +555,7 @@ void qr_thin(MatView<T> A, T* Q, T* R, cudaStream_t st) {
 }
 
 template <typename T>
-void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st) {
+void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st, SvdSide side) {
   if (A.m == 0 || A.n == 0) return;
   // strongly rectangular: reduce to the square triangular factor first so the
   // Jacobi sweeps run over min(m, n) rows instead of max(m, n)
@@ -522,8 +563,9 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st) {
     const int m = A.m, n = A.n;
     DBuf<T> Q((size_t)m * n), R((size_t)n * n), UR((size_t)n * n);
     qr_thin<T>(A, Q.get(), R.get(), st);
-    svd_thin<T>(MatView<T>{R.get(), n, n, n, 1}, UR.get(), S, Vt, st);
-    gemm_rm<T>(false, false, m, n, n, T(1), Q.get(), n, 0, UR.get(), n, 0, T(0), U, n, 0, 1, st);
+    svd_thin<T>(MatView<T>{R.get(), n, n, n, 1}, UR.get(), S, Vt, st, side);
+    if (side != kSvdRight)
+      gemm_rm<T>(false, false, m, n, n, T(1), Q.get(), n, 0, UR.get(), n, 0, T(0), U, n, 0, 1, st);
     return;
   }
   if (A.n >= 2 * A.m) {
@@ -531,8 +573,9 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st) {
     const int m = A.m, n = A.n;
     DBuf<T> Q((size_t)n * m), R((size_t)m * m), VR((size_t)m * m);
     qr_thin<T>(MatView<T>{A.p, n, m, A.cs, A.rs}, Q.get(), R.get(), st);
-    svd_thin<T>(MatView<T>{R.get(), m, m, 1, m}, U, S, VR.get(), st);
-    gemm_rm<T>(false, true, m, n, m, T(1), VR.get(), m, 0, Q.get(), m, 0, T(0), Vt, n, 0, 1, st);
+    svd_thin<T>(MatView<T>{R.get(), m, m, 1, m}, U, S, VR.get(), st, side);
+    if (side != kSvdLeft)
+      gemm_rm<T>(false, true, m, n, m, T(1), VR.get(), m, 0, Q.get(), m, 0, T(0), Vt, n, 0, 1, st);
     return;
   }
   bool tr = A.m < A.n;
@@ -543,13 +586,60 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st) {
     attr_err = cudaFuncSetAttribute(svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmem);
   });
   TT_CUDA(attr_err);
-  const size_t wb = (size_t)m * n * sizeof(T), vb = (size_t)n * n * sizeof(T);
+  // the sweeps orthogonalise the columns of B (A, or A^T when A is wide):
+  // the side they produce directly is U when A is tall, Vt when A is wide
+  const bool need_v = !((side == kSvdLeft && !tr) || (side == kSvdRight && tr));
+  const size_t wb = (size_t)m * n * sizeof(T), vb = need_v ? (size_t)n * n * sizeof(T) : 0;
   const bool w_smem = wb <= kJacobiSmem;
-  const bool v_smem = w_smem && wb + vb <= kJacobiSmem;
+  const bool v_smem = need_v && w_smem && wb + vb <= kJacobiSmem;
   const size_t smem = (w_smem ? wb : 0) + (v_smem ? vb : 0);
-  DBuf<T> Wc(w_smem ? 0 : (size_t)m * n), Vc(v_smem ? 0 : (size_t)n * n);
+  DBuf<T> Wc(w_smem ? 0 : (size_t)m * n), Vc((v_smem || !need_v) ? 0 : (size_t)n * n);
   DBuf<int> perm((size_t)n);
-  svd_kernel<T><<<1, kThreads, smem, st>>>(A, tr, Wc.get(), Vc.get(), w_smem, v_smem, U, S, Vt, perm.get());
+  if constexpr (std::is_same<T, double>::value) {
+    if (n >= kPrecondMinCols) {
+      // FP32 preconditioning: the right singular vectors of an FP32 copy,
+      // made orthonormal in FP64, rotate B to nearly orthogonal columns
+      // W = B V0; the FP64 sweeps on W then converge in one or two sweeps
+      // instead of the six to ten they take from the identity
+      DBuf<double> B64((size_t)m * n), V0((size_t)n * n), W((size_t)m * n), G((size_t)n * n), H((size_t)n * n);
+      DBuf<float> B32((size_t)m * n), U32((size_t)m * n), S32((size_t)n), Vt32((size_t)n * n);
+      // B64 = B row-major (m x n): B = A, or A^T when A is wide
+      if (tr) transpose_view_kernel<double><<<grid_for((long long)m * n), 256, 0, st>>>(A.p, A.rs, A.cs, m, n, B64.get());
+      else transpose_view_kernel<double><<<grid_for((long long)m * n), 256, 0, st>>>(A.p, A.cs, A.rs, m, n, B64.get());
+      count_launch();
+      convert_kernel<double, float><<<grid_for((long long)m * n), 256, 0, st>>>(B64.get(), (long long)m * n, B32.get());
+      count_launch();
+      svd_thin<float>(MatView<float>{B32.get(), m, n, n, 1}, U32.get(), S32.get(), Vt32.get(), st);
+      // V0 = Vt32^T in FP64, then one Newton-Schulz step V0 (3 I - V0^T V0) / 2
+      transpose<float>(n, n, Vt32.get(), U32.get(), st);
+      convert_kernel<float, double><<<grid_for((long long)n * n), 256, 0, st>>>(U32.get(), (long long)n * n, H.get());
+      count_launch();
+      gemm_rm<double>(true, false, n, n, n, 1.0, H.get(), n, 0, H.get(), n, 0, 0.0, G.get(), n, 0, 1, st);
+      newton_schulz_rhs_kernel<<<grid_for((long long)n * n), 256, 0, st>>>(G.get(), n);
+      count_launch();
+      gemm_rm<double>(false, false, n, n, n, 1.0, H.get(), n, 0, G.get(), n, 0, 0.0, V0.get(), n, 0, 1, st);
+      gemm_rm<double>(false, false, m, n, n, 1.0, B64.get(), n, 0, V0.get(), n, 0, 0.0, W.get(), n, 0, 1, st);
+      check_launch("svd preconditioning");
+      MatView<double> wv{W.get(), m, n, n, 1};
+      if (!tr) {
+        svd_kernel<double><<<1, kThreads, smem, st>>>(wv, false, Wc.get(), Vc.get(), w_smem, v_smem, U, S, Vt,
+                                                      perm.get(), V0.get(), need_v);
+        count_launch();
+      } else {
+        // B = A^T = U_B S Vt_B  =>  A = Vt_B^T S U_B^T
+        DBuf<double> UB((size_t)m * n), VtB(need_v ? (size_t)n * n : 0);
+        svd_kernel<double><<<1, kThreads, smem, st>>>(wv, false, Wc.get(), Vc.get(), w_smem, v_smem, UB.get(), S,
+                                                      VtB.get(), perm.get(), V0.get(), need_v);
+        count_launch();
+        if (need_v) transpose<double>(n, n, VtB.get(), U, st);
+        transpose<double>(m, n, UB.get(), Vt, st);
+      }
+      check_launch("svd_kernel");
+      return;
+    }
+  }
+  svd_kernel<T><<<1, kThreads, smem, st>>>(A, tr, Wc.get(), Vc.get(), w_smem, v_smem, U, S, Vt, perm.get(),
+                                           nullptr, need_v);
   count_launch();
   check_launch("svd_kernel");
 }
@@ -625,7 +715,7 @@ void transpose(int m, int n, const T* in, T* out, cudaStream_t st) {
 
 #define INST(T)                                                                 \
   template void qr_thin<T>(MatView<T>, T*, T*, cudaStream_t);                   \
-  template void svd_thin<T>(MatView<T>, T*, T*, T*, cudaStream_t);              \
+  template void svd_thin<T>(MatView<T>, T*, T*, T*, cudaStream_t, SvdSide);     \
   template void lu_solve<T>(int, T*, T*, cudaStream_t);                         \
   template void lu_factor<T>(int, T*, int*, cudaStream_t);                      \
   template void lu_solve_factored<T>(int, const T*, const int*, T*, cudaStream_t); \

@@ -22,8 +22,14 @@ void qr_thin(MatView<T> A, T* Q, T* R, cudaStream_t st);
 // Thin SVD A = U diag(S) Vt by one-sided Jacobi (Hestenes), k = min(m, n),
 // singular values descending; U (m x k), S (k), Vt (k x n) row-major.
 // Single CTA. Returns nothing; the sweep count is bounded (60).
+// Which singular vectors a caller reads: both, only U (left) or only Vt
+// (right). With one side the Jacobi sweeps skip the other side's rotations
+// when the requested side is the one they orthogonalise; the unrequested
+// output is left unspecified.
+enum SvdSide { kSvdBoth = 0, kSvdLeft = 1, kSvdRight = 2 };
+
 template <typename T>
-void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st);
+void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st, SvdSide side = kSvdBoth);
 
 // Solves A x = b in place (A n x n row-major, destroyed; b n-vector becomes x)
 // by LU with partial pivoting, right-looking and blocked (panel width 32).

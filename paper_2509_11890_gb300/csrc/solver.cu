@@ -189,9 +189,10 @@ int truncation_rank_rel(const std::vector<double>& s, double tol_rel, int cap) {
 // ---------------------------------------------------------------------------
 // Thin SVD of a row-major matrix; the mixed precisions run the Jacobi sweeps
 // in FP32 (the block-index move only needs the truncation-level spectrum).
-void svd_prec(int prec, MatView<double> A, double* U, double* S, double* Vt, cudaStream_t st) {
+void svd_prec(int prec, MatView<double> A, double* U, double* S, double* Vt, cudaStream_t st,
+              SvdSide side = kSvdBoth) {
   if (prec == TT_FP64) {
-    svd_thin<double>(A, U, S, Vt, st);
+    svd_thin<double>(A, U, S, Vt, st, side);
     return;
   }
   const int m = A.m, n = A.n, k = m < n ? m : n;
@@ -199,10 +200,10 @@ void svd_prec(int prec, MatView<double> A, double* U, double* S, double* Vt, cud
   DBuf<double> dense((size_t)m * n);
   dev_copy2d(dense.get(), n, A.p, A.rs, m, n, 1.0, st);  // A is row-major here (cs == 1)
   to_f32(dense.get(), a.get(), (size_t)m * n, st);
-  svd_thin<float>(MatView<float>{a.get(), m, n, n, 1}, u.get(), s.get(), vt.get(), st);
-  to_f64(u.get(), U, (size_t)m * k, st);
+  svd_thin<float>(MatView<float>{a.get(), m, n, n, 1}, u.get(), s.get(), vt.get(), st, side);
+  if (side != kSvdRight) to_f64(u.get(), U, (size_t)m * k, st);
   to_f64(s.get(), S, k, st);
-  to_f64(vt.get(), Vt, (size_t)k * n, st);
+  if (side != kSvdLeft) to_f64(vt.get(), Vt, (size_t)k * n, st);
 }
 
 // Dense local solve K x = b (K destroyed, b becomes x). The mixed precisions
@@ -283,6 +284,8 @@ struct AmenInfo {
   long long gmres_iters = 0;
   double forcing = 0.0;        // largest FP64 relative residual of a local solve
   long long corrections = 0;   // correction solves the forcing check asked for
+  bool converged = false;      // the sweeps met their tolerance within the budget (in a
+                               // reduced precision: max(tol, the precision's floor))
 };
 
 // Restarted GMRES (Saad & Schultz) on device vectors with classical
@@ -377,7 +380,7 @@ double sweep_floor(int prec) {
 }
 
 // FP64 sweeps that refine a direction found in a reduced precision
-constexpr int kRefineSweeps = 2;
+constexpr int kRefineSweeps = 1;
 
 BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap, int kick, int max_sweeps,
                    Counter& rnd, int prec_in, int dense_max, int gmres_restart, int gmres_maxit, AmenInfo* info) {
@@ -592,7 +595,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
           dev_copy2d(mat.get() + bb * rr, cols, nw->get() + bb * n, rr, rows, rr, 1.0, st);
         int kk = std::min(rows, cols);
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
-        svd_prec(prec, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+        svd_prec(prec, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st, kSvdLeft);
         std::vector<double> hs = host_copy(S.get(), kk);
         int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(rows - keep, std::max(cap - keep, 0)));
@@ -636,7 +639,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         const int rows = nblk * rl, cols = 4 * rr;
         int kk = std::min(rows, cols);
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
-        svd_prec(prec, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+        svd_prec(prec, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st, kSvdRight);
         std::vector<double> hs = host_copy(S.get(), kk);
         int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(cols - keep, std::max(cap - keep, 0)));
@@ -681,11 +684,14 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
     }
     if (prec_in == TT_FP64) {
       if (sweep >= 1 && max_change < tol) {
+        info->converged = true;
         ++sweep;
         break;
       }
     } else if (prec != TT_FP64) {
-      if ((sweep >= 1 && max_change < std::max(tol, sweep_floor(prec_in))) || sweep + 1 >= max_sweeps) {
+      const bool stalled = sweep >= 1 && max_change < std::max(tol, sweep_floor(prec_in));
+      if (stalled) info->converged = true;
+      if (stalled || sweep + 1 >= max_sweeps) {
         // switch to FP64: rebuild the environments the next sweep reads
         prec = TT_FP64;
         if (forward) {
@@ -797,7 +803,7 @@ static double local_min_eig(int nl, const double* Mk, const double* Dk, double* 
   dev_axpy(Sh.get(), dI.get(), nn, 1.0, st);
   DBuf<float> Sf(nn), U(nn), Sv(nl), Vt(nn);
   to_f32(Sh.get(), Sf.get(), nn, st);
-  svd_thin<float>(MatView<float>{Sf.get(), nl, nl, nl, 1}, U.get(), Sv.get(), Vt.get(), st);
+  svd_thin<float>(MatView<float>{Sf.get(), nl, nl, nl, 1}, U.get(), Sv.get(), Vt.get(), st, kSvdLeft);
   DBuf<double> v(nl), Sv64(nl);
   transpose<float>(nl, nl, U.get(), Vt.get(), st);  // row nl-1 of U^T = last column of U
   to_f64(Vt.get() + (size_t)(nl - 1) * nl, v.get(), nl, st);
@@ -1001,7 +1007,8 @@ double min_gen_eig_dmrg(const DTT& M, const DTT& dM, DTT* e_io, bool warm, Count
       const int rows = rl * nmode, cols = nmode * rr;
       const int kk = std::min(rows, cols);
       DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
-      svd_thin<double>(MatView<double>{x.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+      svd_thin<double>(MatView<double>{x.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
+                       forward ? kSvdLeft : kSvdRight);
       const int keep = dmrg_keep(host_copy(S.get(), kk), tol, rank);
       const int extra = std::max(0, std::min(rank, kk) - keep);
       const int nk = keep + extra;
@@ -1244,7 +1251,7 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
   corrections_ += info.corrections;
   w_ = std::make_unique<BlockTT>(w);
   *sweeps = info.sweeps;
-  amen_ok_ = info.max_change < eta_;
+  amen_ok_ = info.converged;
   dX = unvec(w.component(0));
   dY = unvec(w.component(1));
   if (p_.ineq) {

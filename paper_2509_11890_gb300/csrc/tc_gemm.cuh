@@ -18,8 +18,10 @@ bool tc_stage2(int prec, long long rw, long long R, long long R2, long long m, l
 // both operands K-major in the given element type (TT_MIXED_TF32: fp32 storage
 // read as TF32; TT_MIXED_BF16: bf16 storage). Used by stage 2 and by the
 // benchmark's kernel timing.
+// stat_flops > 0: the launches are timed with CUDA events and counted with
+// that many algorithmic flops in the tensor-core statistics
 void tc_gemm_tn(int prec, int M, int N, int K, int batch, const void* A, long long sA,
-                const void* B, long long sB, float* C, long long sC, cudaStream_t st);
+                const void* B, long long sB, float* C, long long sC, cudaStream_t st, double stat_flops = 0.0);
 
 // C (M x N, fp64) = A (M x K, fp64, row stride lda) B (N x K, fp64, row stride
 // ldb)^T with the product on the TF32 tensor cores (operands rounded to TF32,

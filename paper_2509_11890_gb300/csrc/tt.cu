@@ -697,7 +697,7 @@ std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* 
     MatView<double> v{t.core(k), rows, r2, r2, 1};
     {
       ProfScope ps("round.svd");
-      svd_thin<double>(v, U.get(), S.get(), Vt.get(), st);
+      svd_thin<double>(v, U.get(), S.get(), Vt.get(), st, kSvdLeft);
     }
     std::vector<double> hs(kk);
     TT_CUDA(cudaMemcpyAsync(hs.data(), S.get(), kk * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -712,8 +712,9 @@ std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* 
     if (hook && hook->prev && (int)hook->prev->size() > k + 1) (*hook->prev)[k + 1] = keep;
     auto nc = std::make_shared<DBuf<double>>((size_t)rows * keep);
     dev_copy2d(nc->get(), keep, U.get(), kk, rows, keep, 1.0, st);
-    // next core <- diag(S[:keep]) Vt[:keep] core_{k+1}
-    dev_scale_rows(Vt.get(), keep, r2, S.get(), st);
+    // next core <- diag(S[:keep]) Vt[:keep] core_{k+1}, with diag(S) Vt = U^T A
+    gemm_rm<double>(true, false, keep, r2, rows, 1.0, U.get(), kk, 0, t.core(k), r2, 0, 0.0, Vt.get(), r2, 0, 1,
+                    st);
     int r3 = t.r[k + 2];
     auto xc = std::make_shared<DBuf<double>>((size_t)keep * M * r3);
     gemm_rm<double>(false, false, keep, M * r3, r2, 1.0, Vt.get(), r2, 0, t.core(k + 1), M * r3, 0, 0.0,

@@ -118,7 +118,7 @@ def test_hadamard_matvec_inner():
     assert math.isclose(val, tt.inner(u, w), rel_tol=1e-11, abs_tol=1e-11)
 
 
-@pytest.mark.parametrize("d,rk,seed", [(5, 6, 30), (8, 12, 31), (10, 20, 32)])
+@pytest.mark.parametrize("d,rk,seed", [(5, 6, 30), (8, 12, 31), (10, 20, 32), (6, 48, 33), (7, 40, 34)])
 def test_round_ranks_and_error(d, rk, seed):
     base = _rtt([4] * d, max(2, rk // 3), seed)
     noise = tt.scale(_rtt([4] * d, rk, seed + 100), 1e-6)
