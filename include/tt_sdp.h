@@ -227,6 +227,11 @@ typedef struct {
   int32_t gmres_max_iters; /* operator products per local solve                       */
   int32_t eig_two_site;    /* step lengths (Section 3.4): 1 two-site DMRG sweeps with
                               SVD rank adaptation and random kicks, 0 one-site ALS    */
+  double time_limit;       /* tt_sdp_solve / tt_sdp_solve_batch: wall-clock seconds per
+                              solve (0: none). When it passes, the iteration in
+                              progress is abandoned at its next core step, the
+                              context keeps the last completed iterate and the solve
+                              returns TT_E_NO_CONVERGENCE                          */
 } tt_sdp_options;
 
 typedef struct tt_sdp_ctx tt_sdp_ctx;

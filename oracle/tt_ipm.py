@@ -323,21 +323,28 @@ def amen_solve(data: NewtonData, d: int, w0: BlockTT | None, tol: float, cap: in
         info["max_change"] = max_change
         if sweep >= 1 and max_change < tol:
             break
-    # bring the block index back to core 0 without truncation (for warm starts)
+    # the solution, exact, with the block index where the last sweep left it
     pos = d - 1 if (info["sweeps"] % 2 == 1) else 0
-    cores = [c.copy() for c in frame]
+    sol = BlockTT(cores=[c.copy() for c in frame], block=block, pos=pos)
+    sol.cores[pos] = block[0]
+    info["ranks"] = tt.ranks(sol.cores)
+    # the warm start of the next solve has its block index at core 0: moving it
+    # there is a sweep of block moves, truncated like the sweeps' moves (the
+    # frame would otherwise grow to nblk times its rank)
+    warm = sol
     if pos == d - 1:
+        cores = [c.copy() for c in frame]
         for k in range(d - 1, 0, -1):
             rl, m, rr = block.shape[1:]
             mat = block.reshape(nblk * rl, m * rr)
-            q, r = np.linalg.qr(mat.T)
-            cores[k] = q.T.reshape(-1, m, rr)
-            coef = r.T.reshape(nblk, rl, -1)
+            u, sv, vt = np.linalg.svd(mat, full_matrices=False)
+            keep = _truncation_rank_rel(sv, tol / math.sqrt(d), cap)
+            cores[k] = vt[:keep].reshape(keep, m, rr)
+            coef = (u[:, :keep] * sv[:keep]).reshape(nblk, rl, keep)
             block = np.einsum("xja,bac->bxjc", cores[k - 1], coef)
-    cores[0] = block[0]
-    out = BlockTT(cores=cores, block=block, pos=0)
-    info["ranks"] = tt.ranks(cores)
-    return out, info
+        cores[0] = block[0]
+        warm = BlockTT(cores=cores, block=block, pos=0)
+    return sol, warm, info
 
 
 # ----------------------------------------------------------------------------
@@ -715,9 +722,9 @@ class TTIPM:
 
     def direction(self, direction, sigma_mu, corr, zero_p, zero_d):
         data = self.newton_data(direction, sigma_mu, corr, zero_p, zero_d)
-        w, info = amen_solve(data, self.d, self.w, self.eta, self.o.rank_cap, self.o.kick,
+        w, warm, info = amen_solve(data, self.d, self.w, self.eta, self.o.rank_cap, self.o.kick,
                              self.o.max_sweeps, self.rnd)
-        self.w = w
+        self.w = warm
         comps = [tt.unvec_tt(w.component(b)) for b in range(data.nblk)]
         if data.nblk == 3:
             dX, dY, dZ = comps

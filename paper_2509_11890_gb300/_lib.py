@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
                 ("precision", c_int32), ("max_iters", c_int32), ("max_sweeps", c_int32), ("kick", c_int32),
                 ("eig_rank", c_int32), ("eig_sweeps", c_int32), ("seed", ctypes.c_uint64),
                 ("local_dense_max", c_int32), ("gmres_restart", c_int32), ("gmres_max_iters", c_int32),
-                ("eig_two_site", c_int32)]
+                ("eig_two_site", c_int32), ("time_limit", c_double)]
 
 
 class IterInfo(ctypes.Structure):

@@ -103,6 +103,8 @@ Options to_options(const tt_sdp_options* o) {
   r.gmres_restart = o->gmres_restart;
   r.gmres_max_iters = o->gmres_max_iters;
   r.eig_two_site = o->eig_two_site;
+  r.time_limit = o->time_limit;
+  TT_CHECK(r.time_limit >= 0.0, TT_E_INVALID_ARG, "time_limit must be >= 0");
   TT_CHECK(r.eig_two_site == 0 || r.eig_two_site == 1, TT_E_INVALID_ARG, "eig_two_site must be 0 or 1");
   TT_CHECK(r.local_dense_max >= 0 && r.gmres_restart > 0 && r.gmres_max_iters > 0, TT_E_INVALID_ARG,
            "invalid local solver options");
@@ -303,6 +305,7 @@ void tt_sdp_default_options(tt_sdp_options* o) {
   o->gmres_restart = 40;
   o->gmres_max_iters = 400;
   o->eig_two_site = 1;
+  o->time_limit = 0.0;
 }
 
 static tt_status make_ctx(Problem p, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
@@ -412,9 +415,7 @@ tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info) {
   });
 }
 
-tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out) {
-  if (!ctx || !out) return TT_E_INVALID_ARG;
-  std::memset(out, 0, sizeof(*out));
+static tt_status solve_loop(tt_sdp_ctx* ctx, tt_sdp_result* out) {
   tt_sdp_iter_info info;
   double secs = 0.0;
   const int max_iters = ctx->solver->options().max_iters;
@@ -439,6 +440,15 @@ tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out) {
   }
   out->status = TT_E_NO_CONVERGENCE;
   return TT_E_NO_CONVERGENCE;
+}
+
+tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out) {
+  if (!ctx || !out) return TT_E_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  ctx->solver->set_deadline(ctx->solver->options().time_limit);
+  const tt_status s = solve_loop(ctx, out);
+  ctx->solver->set_deadline(0.0);
+  return s;
 }
 
 tt_status tt_sdp_get_iterate(tt_sdp_ctx* ctx, int32_t which, int32_t* ranks, double* cores, size_t* count) {

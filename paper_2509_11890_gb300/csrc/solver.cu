@@ -382,8 +382,12 @@ double sweep_floor(int prec) {
 // FP64 sweeps that refine a direction found in a reduced precision
 constexpr int kRefineSweeps = 1;
 
+// Returns the solution with the block index at the core where the last
+// sweep ended; *warm receives the same solution moved to core 0 (truncated)
+// as the warm start of the next solve.
 BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap, int kick, int max_sweeps,
-                   Counter& rnd, int prec_in, int dense_max, int gmres_restart, int gmres_maxit, AmenInfo* info) {
+                   Counter& rnd, int prec_in, int dense_max, int gmres_restart, int gmres_maxit, AmenInfo* info,
+                   BlockTT* warm, const std::chrono::steady_clock::time_point* deadline) {
   // sweeps run in prec_in until they stall at its floor (or use the sweep
   // budget), then up to kRefineSweeps FP64 sweeps refine the direction with
   // FP64 environments, local operators and solves
@@ -431,6 +435,8 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
     const bool forward = sweep % 2 == 0;
     max_change = 0.0;
     for (int step = 0; step < d; ++step) {
+      TT_CHECK(!deadline || std::chrono::steady_clock::now() < *deadline, TT_E_NO_CONVERGENCE,
+               "time limit reached");
       const int k = forward ? step : d - 1 - step;
       const int rl = frame.r[k], rr = frame.r[k + 1];
       const size_t n = (size_t)rl * 4 * rr;
@@ -710,50 +716,60 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
   }
   info->sweeps = sweep;
   info->max_change = max_change;
-  // bring the block index back to core 0 without truncation
+  // the solution, exact, with the block index where the last sweep left it
   const bool at_end = (sweep % 2 == 1);
+  BlockTT sol;
+  sol.frame = frame;
+  sol.nblk = nblk;
+  sol.block = block;
+  sol.pos = at_end ? d - 1 : 0;
+  *warm = sol;
   if (at_end) {
+    // the warm start of the next solve has its block index at core 0: moving
+    // it there is a sweep of block moves truncated like the sweeps' moves
+    // (without truncation the frame would grow to nblk times its rank)
     for (int k = d - 1; k >= 1; --k) {
       int rl = frame.r[k], rr = frame.r[k + 1];
       int rows = nblk * rl, cols = 4 * rr;
       int kk = std::min(rows, cols);
-      // QR of mat^T (cols x rows)
-      DBuf<double> Q((size_t)cols * kk), R((size_t)kk * rows);
-      qr_thin<double>(MatView<double>{block->get(), cols, rows, 1, cols}, Q.get(), R.get(), st);
-      auto fk = std::make_shared<DBuf<double>>((size_t)kk * cols);
-      transpose<double>(cols, kk, Q.get(), fk->get(), st);
+      DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
+      svd_thin<double>(MatView<double>{block->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
+      std::vector<double> hs = host_copy(S.get(), kk);
+      const int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
+      auto fk = std::make_shared<DBuf<double>>((size_t)keep * cols);
+      dev_copy(fk->get(), Vt.get(), (size_t)keep * cols, st);
       frame.c[k] = fk;
-      frame.r[k] = kk;
-      // coef[b][a][c] = R^T[(b a)][c] ; new block[b] = frame[k-1] coef[b]
-      DBuf<double> RT((size_t)rows * kk);
-      transpose<double>(kk, rows, R.get(), RT.get(), st);
+      frame.r[k] = keep;
+      // coef[b][a][c] = U[(b a)][c] S[c]; new block[b] = frame[k-1] coef[b]
+      DBuf<double> coef((size_t)rows * keep);
+      dev_copy2d(coef.get(), keep, U.get(), kk, rows, keep, 1.0, st);
+      dev_scale_cols(coef.get(), rows, keep, S.get(), st);
       int rp = frame.r[k - 1];
-      size_t nn = (size_t)rp * 4 * kk;
+      size_t nn = (size_t)rp * 4 * keep;
       auto nb2 = std::make_shared<DBuf<double>>(nblk * nn);
       for (int bb = 0; bb < nblk; ++bb)
-        gemm_rm<double>(false, false, rp * 4, kk, rl, 1.0, frame.core(k - 1), rl, 0, RT.get() + (size_t)bb * rl * kk,
-                        kk, 0, 0.0, nb2->get() + bb * nn, kk, 0, 1, st);
+        gemm_rm<double>(false, false, rp * 4, keep, rl, 1.0, frame.core(k - 1), rl, 0,
+                        coef.get() + (size_t)bb * rl * keep, keep, 0, 0.0, nb2->get() + bb * nn, keep, 0, 1, st);
       auto c1 = std::make_shared<DBuf<double>>(nn);
       dev_copy(c1->get(), nb2->get(), nn, st);
       frame.c[k - 1] = c1;
       block = nb2;
     }
+    warm->frame = frame;
+    warm->block = block;
+    warm->pos = 0;
   }
-  BlockTT out;
-  out.frame = frame;
-  out.nblk = nblk;
-  out.block = block;
-  return out;
+  return sol;
 }
 
 }  // namespace
 
 DTT BlockTT::component(int b) const {
   DTT t = frame;
-  size_t n0 = frame.csize(0);
+  size_t n0 = frame.csize(pos);
   auto c0 = std::make_shared<DBuf<double>>(n0);
   dev_copy(c0->get(), block->get() + b * n0, n0, cur_stream());
-  t.c[0] = c0;
+  t.c[pos] = c0;
   return t;
 }
 
@@ -1147,6 +1163,14 @@ static double gen_eig(const Options& o, const DTT& M, const DTT& dM, DTT* e, boo
   return min_gen_eig(M, dM, e, warm, rnd, rank, sweeps, TT_FP64);
 }
 
+void Solver::set_deadline(double seconds_from_now) {
+  has_deadline_ = seconds_from_now > 0.0;
+  if (has_deadline_)
+    deadline_ = std::chrono::steady_clock::now() +
+                std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                    std::chrono::duration<double>(seconds_from_now));
+}
+
 Solver::~Solver() {
   for (cudaStream_t s : side_) {
     cudaStreamSynchronize(s);
@@ -1244,12 +1268,14 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
     if (ct) nd.rt.push_back({1.0, tt_diag(vecv(*ct)), *cs});
   }
   AmenInfo info;
+  BlockTT warm;
   BlockTT w = amen_solve(nd, d, w_ ? w_.get() : nullptr, eta_, o_.rank_cap, o_.kick, o_.max_sweeps, rnd_,
-                         o_.prec, o_.local_dense_max, o_.gmres_restart, o_.gmres_max_iters, &info);
+                         o_.prec, o_.local_dense_max, o_.gmres_restart, o_.gmres_max_iters, &info, &warm,
+                         has_deadline_ ? &deadline_ : nullptr);
   gmres_iters_ += info.gmres_iters;
   forcing_it_ = std::max(forcing_it_, info.forcing);
   corrections_ += info.corrections;
-  w_ = std::make_unique<BlockTT>(w);
+  w_ = std::make_unique<BlockTT>(warm);
   *sweeps = info.sweeps;
   amen_ok_ = info.converged;
   dX = unvec(w.component(0));

@@ -2,6 +2,8 @@
 // Newton solves (Section 3.3), step lengths (Section 3.4) and Algorithm 1.
 #pragma once
 
+#include <chrono>
+
 #include <memory>
 #include <string>
 #include <vector>
@@ -26,9 +28,10 @@ Problem build_cc(const DTT& c_plus, const DTT& c_minus, const DTT& adjacency);
 
 // Block TT (Definition "Block Tensor-Train") with the block index at core 0.
 struct BlockTT {
-  DTT frame;                              // vector TT (mode 4); core 0 = block 0
+  DTT frame;                              // vector TT (mode 4); core pos = block 0
   int nblk = 0;
-  std::shared_ptr<DBuf<double>> block;    // nblk x r0 x 4 x r1
+  int pos = 0;                            // core that carries the block index
+  std::shared_ptr<DBuf<double>> block;    // nblk x r_pos x 4 x r_pos+1
   DTT component(int b) const;
 };
 
@@ -40,6 +43,7 @@ struct Options {
   int prec = 0;
   int max_iters = 60, max_sweeps = 4, kick = 4, eig_rank = 4, eig_sweeps = 4;
   int eig_two_site = 1;  // step lengths by two-site DMRG sweeps; 0: one-site ALS
+  double time_limit = 0.0;  // seconds per solve (0: none)
   uint64_t seed = 1234;
   int local_dense_max = 4096, gmres_restart = 40, gmres_max_iters = 400;
 };
@@ -66,6 +70,9 @@ class Solver {
   Solver(const Solver&) = delete;
   Solver& operator=(const Solver&) = delete;
   IterLog iterate();        // one iteration of Algorithm 1
+  // wall-clock deadline checked between the core steps of the AMEn sweeps;
+  // past it the iteration in progress throws TT_E_NO_CONVERGENCE
+  void set_deadline(double seconds_from_now);
   const DTT& X() const { return X_; }
   const DTT& Y() const { return Y_; }
   const DTT& T() const { return T_; }
@@ -132,6 +139,8 @@ class Solver {
   DTT eX_, eZ_, eT_, eS_;
   bool haveX_ = false, haveZ_ = false, haveT_ = false, haveS_ = false;
   std::vector<cudaStream_t> side_;  // streams of the concurrent roundings
+  bool has_deadline_ = false;
+  std::chrono::steady_clock::time_point deadline_;
 };
 
 // min over e of <e, dM e>/<e, M e> (M positive definite): one-site ALS and

@@ -41,6 +41,11 @@ __global__ void scale_rows_kernel(double* a, int rows, int cols, const double* s
   GRID_LOOP(e, n) a[e] *= s[e / cols];
 }
 
+__global__ void scale_cols_kernel(double* a, int rows, int cols, const double* s) {
+  long long n = (long long)rows * cols;
+  GRID_LOOP(e, n) a[e] *= s[e % cols];
+}
+
 // dst core [R][M][R2], place alpha * src [r][M][r2] at rank offsets (o1, o2)
 __global__ void place_kernel(double* dst, int R, int M, int R2, const double* src, int r, int r2,
                              int o1, int o2, double alpha) {
@@ -236,6 +241,12 @@ void dev_scale_rows(double* a, int rows, int cols, const double* s, cudaStream_t
   scale_rows_kernel<<<grid1((long long)rows * cols), 256, 0, st>>>(a, rows, cols, s);
   count_launch();
   check_launch("scale_rows");
+}
+void dev_scale_cols(double* a, int rows, int cols, const double* s, cudaStream_t st) {
+  if ((long long)rows * cols == 0) return;
+  scale_cols_kernel<<<grid1((long long)rows * cols), 256, 0, st>>>(a, rows, cols, s);
+  count_launch();
+  check_launch("scale_cols");
 }
 void dev_multi_dot(const double* V, int nvec, size_t N, const double* w, double* out, cudaStream_t st) {
   if (nvec <= 0) return;

@@ -110,6 +110,7 @@ void dev_copy(double* dst, const double* src, size_t n, cudaStream_t st);
 void dev_copy2d(double* dst, long long dld, const double* src, long long sld, int rows, int cols,
                 double alpha, cudaStream_t st);
 void dev_scale_rows(double* a, int rows, int cols, const double* s, cudaStream_t st);
+void dev_scale_cols(double* a, int rows, int cols, const double* s, cudaStream_t st);
 double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st);
 // out[i] = <V_i, w> for the rows of a row-major nvec x N matrix (device output)
 void dev_multi_dot(const double* V, int nvec, size_t N, const double* w, double* out, cudaStream_t st);

@@ -130,3 +130,17 @@ def test_forcing_check_reports_fp64_local_residuals(prec, dense_max):
         if dense_max > 0:
             assert info["forcing"] <= 1e-6, info
     assert info["forcing_corrections"] >= 0
+
+
+def test_time_limit_stops_a_solve_and_keeps_the_last_iterate():
+    inst = inputs.maxcut_kron(5, 1)
+    ctx = tg.Context.maxcut(inst["adjacency_cores"], _opts(time_limit=1e-3))
+    res = ctx.solve()
+    assert res["status"] == 7, res          # TT_E_NO_CONVERGENCE: the limit passed
+    X = tt.full_mat(ctx.iterate(0))         # the context is still usable
+    assert np.all(np.isfinite(X))
+    # without a limit the same context continues to the optimum
+    ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]))
+    ctx2 = tg.Context.maxcut(inst["adjacency_cores"], _opts())
+    res2 = ctx2.solve()
+    assert res2["status"] == 0 and abs(res2["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3

@@ -38,7 +38,7 @@ def test_amen_direction_equals_dense_newton(direction):
     (dX, dY, dZ), K, R = sd.newton_solve(pad, X, Y, Z, mu=mu, direction=direction, sigma=0.5)
     sig_mu = 0.5 * mu
     data = ipm.newton_data(direction, sig_mu, None, False, False)
-    w, info = tt_ipm.amen_solve(data, d, None, 1e-12, 64, 4, 8, ipm.rnd)
+    w, _, info = tt_ipm.amen_solve(data, d, None, 1e-12, 64, 4, 8, ipm.rnd)
     got = [tt.full_mat(tt.unvec_tt(w.component(b))) for b in range(3)]
     for a, b in zip(got, (dX, dY, dZ)):
         np.testing.assert_allclose(a, b, atol=1e-8 * (1 + np.abs(b).max()))
@@ -56,7 +56,7 @@ def test_amen_truncated_direction_meets_forcing():
     mu = ipm.mu()
     eta = 1e-3
     data = ipm.newton_data("aho", mu, None, False, False)
-    w, info = tt_ipm.amen_solve(data, d, None, eta, 16, 2, 6, ipm.rnd)
+    w, _, info = tt_ipm.amen_solve(data, d, None, eta, 16, 2, 6, ipm.rnd)
     X, Y, Z = (tt.full_mat(m) for m in (ipm.X, ipm.Y, ipm.Z))
     K, R = sd.newton_system(sd.padded_maxcut(inst["weights"]), X, Y, Z, mu=mu, direction="aho", sigma=1.0)
     du = np.concatenate([tt.full_vec(w.component(b)) for b in range(3)])
