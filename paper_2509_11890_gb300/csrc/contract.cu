@@ -5,6 +5,7 @@
 //   stage 3  contract with the frame core (or the other environment).
 // FP64 runs the stages in FP64; FP32 converts the operands once and runs
 // the same stages in FP32 with FP32 accumulation.
+#include <memory>
 #include <mutex>
 
 #include "contract.cuh"
@@ -328,26 +329,36 @@ void local_matrix(const CDims& d, const double* phi, const double* op, const dou
 // ---------------------------------------------------------------------------
 
 namespace {
+// Each host thread keeps its own records (threads that solve contexts
+// concurrently never wait on one another here); readers visit every thread's
+// records through a registry.
 struct Stats {
-  std::mutex mu;
+  std::mutex mu;  // taken by the owning thread and by readers
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  std::pair<cudaEvent_t, cudaEvent_t> open_ev{nullptr, nullptr};
+  bool open = false;
   double flops = 0.0, seconds = 0.0;
   unsigned long long calls = 0;
 };
-Stats& stats(int key) {
-  static Stats s[2];
-  return s[key & 1];
-}
-// the event pair a thread has opened and not yet closed, per key (threads that
-// solve contexts concurrently each time their own contractions)
-struct OpenPair {
-  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-  bool open = false;
+struct Registry {
+  std::mutex mu;
+  std::vector<std::shared_ptr<Stats>> all[2];
 };
-OpenPair& open_pair(int key) {
-  static thread_local OpenPair o[2];
-  return o[key & 1];
+Registry& registry() {
+  static Registry r;
+  return r;
+}
+Stats& stats(int key) {
+  static thread_local std::shared_ptr<Stats> mine[2];
+  std::shared_ptr<Stats>& m = mine[key & 1];
+  if (!m) {
+    m = std::make_shared<Stats>();
+    Registry& r = registry();
+    std::lock_guard<std::mutex> lk(r.mu);
+    r.all[key & 1].push_back(m);
+  }
+  return *m;
 }
 void resolve(Stats& s) {
   for (auto& ev : s.pending) {
@@ -372,44 +383,52 @@ void stats_begin(cudaStream_t st, int key) {
     TT_CUDA(cudaEventCreate(&ev.first));
     TT_CUDA(cudaEventCreate(&ev.second));
   }
-  OpenPair& o = open_pair(key);
-  if (o.open) s.pool.push_back(o.ev);  // a begin without an end (an exception in between)
+  if (s.open) s.pool.push_back(s.open_ev);  // a begin without an end (an exception in between)
   TT_CUDA(cudaEventRecord(ev.first, st));
-  o.ev = ev;
-  o.open = true;
+  s.open_ev = ev;
+  s.open = true;
 }
 
 void stats_end(cudaStream_t st, double flops, int key) {
   Stats& s = stats(key);
   std::lock_guard<std::mutex> lk(s.mu);
-  OpenPair& o = open_pair(key);
-  if (!o.open) return;
-  TT_CUDA(cudaEventRecord(o.ev.second, st));
-  o.open = false;
-  s.pending.push_back(o.ev);
+  if (!s.open) return;
+  TT_CUDA(cudaEventRecord(s.open_ev.second, st));
+  s.open = false;
+  s.pending.push_back(s.open_ev);
   s.flops += flops;
   ++s.calls;
   if (s.pending.size() > 4096) resolve(s);
 }
 
 void stats_read(double* flops, double* seconds, int key, unsigned long long* calls) {
-  Stats& s = stats(key);
-  std::lock_guard<std::mutex> lk(s.mu);
-  resolve(s);
-  if (flops) *flops = s.flops;
-  if (seconds) *seconds = s.seconds;
-  if (calls) *calls = s.calls;
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  double f = 0.0, sec = 0.0;
+  unsigned long long c = 0;
+  for (auto& sp : r.all[key & 1]) {
+    std::lock_guard<std::mutex> lk2(sp->mu);
+    resolve(*sp);
+    f += sp->flops;
+    sec += sp->seconds;
+    c += sp->calls;
+  }
+  if (flops) *flops = f;
+  if (seconds) *seconds = sec;
+  if (calls) *calls = c;
 }
 
 void stats_reset() {
-  for (int key = 0; key < 2; ++key) {
-    Stats& s = stats(key);
-    std::lock_guard<std::mutex> lk(s.mu);
-    resolve(s);
-    s.flops = 0.0;
-    s.seconds = 0.0;
-    s.calls = 0;
-  }
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  for (int key = 0; key < 2; ++key)
+    for (auto& sp : r.all[key]) {
+      std::lock_guard<std::mutex> lk2(sp->mu);
+      resolve(*sp);
+      sp->flops = 0.0;
+      sp->seconds = 0.0;
+      sp->calls = 0;
+    }
 }
 
 }  // namespace ttsdp

@@ -601,7 +601,10 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
           dev_copy2d(mat.get() + bb * rr, cols, nw->get() + bb * n, rr, rows, rr, 1.0, st);
         int kk = std::min(rows, cols);
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
-        svd_prec(prec, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st, kSvdLeft);
+        // the SVD only chooses the next frame's subspace: it runs in the solve's
+        // reduced precision even in the FP64 refinement sweep
+        svd_prec(prec_in, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
+                 kSvdLeft);
         std::vector<double> hs = host_copy(S.get(), kk);
         int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(rows - keep, std::max(cap - keep, 0)));
@@ -610,7 +613,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         dev_copy2d(u.get(), nk, U.get(), kk, rows, keep, 1.0, st);
         // with a kick, or when the SVD ran in FP32, the new frame core is
         // re-orthonormalised in FP64 (the SVD only chooses the subspace)
-        if (extra > 0 || prec != TT_FP64) {
+        if (extra > 0 || prec_in != TT_FP64) {
           if (extra > 0) {
             std::vector<double> rndv = rnd.draw((size_t)rows * extra);
             DBuf<double> rr_((size_t)rows * extra);
@@ -645,7 +648,8 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         const int rows = nblk * rl, cols = 4 * rr;
         int kk = std::min(rows, cols);
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
-        svd_prec(prec, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st, kSvdRight);
+        svd_prec(prec_in, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
+                 kSvdRight);
         std::vector<double> hs = host_copy(S.get(), kk);
         int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(cols - keep, std::max(cap - keep, 0)));
@@ -656,7 +660,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         DBuf<double> vk((size_t)cols * keep);
         transpose<double>(keep, cols, vt_keep.get(), vk.get(), st);
         dev_copy2d(v.get(), nk, vk.get(), keep, cols, keep, 1.0, st);
-        if (extra > 0 || prec != TT_FP64) {
+        if (extra > 0 || prec_in != TT_FP64) {
           if (extra > 0) {
             std::vector<double> rndv = rnd.draw((size_t)cols * extra);
             DBuf<double> rr_((size_t)cols * extra);
