@@ -31,6 +31,11 @@ void keep_pool_memory() {
   if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    // a block freed on one stream is not handed to another stream behind an
+    // inserted wait: with many streams (concurrent solves) such waits chain
+    // the streams together; the pool grows instead
+    int no = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   }
   done_for = dev;
 }
@@ -264,7 +269,7 @@ tt_status tt_round(const tt_desc* in, double delta, int32_t rank_cap, int32_t* r
     tt_to_device(rz.first, cores_out);
     for (int k = 0; k <= rz.first.d; ++k) ranks_out[k] = rz.first.r[k];
     *zeta_out = rz.second;
-    TT_CUDA(cudaStreamSynchronize(cur_stream()));
+    TT_CUDA(sync_stream(cur_stream()));
   });
 }
 
@@ -475,7 +480,7 @@ void tt_sdp_destroy(tt_sdp_ctx* ctx) {
   try {
     StreamGuard g(ctx->stream);
     ctx->solver.reset();
-    cudaStreamSynchronize(ctx->stream);
+    sync_stream(ctx->stream);
   } catch (...) {
   }
   delete ctx;
@@ -610,11 +615,17 @@ extern "C" tt_status tt_sdp_solve_batch(int32_t n, tt_sdp_ctx* const* ctxs, int3
     if (!ctxs[i]) return TT_E_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TT_E_CUDA;
-  for (int i = 0; i < n; ++i) cudaStreamSynchronize(ctxs[i]->stream);  // creation work is complete
+  for (int i = 0; i < n; ++i) sync_stream(ctxs[i]->stream);  // creation work is complete
   std::atomic<int> next{0};
   std::vector<tt_status> st(n, TT_OK);
   std::vector<std::thread> pool;
   const int nw = workers < n ? workers : (n > 0 ? n : 1);
+  // while the workers run, waits sleep and each solve stays on one thread
+  struct Active {
+    int k;
+    explicit Active(int k_) : k(k_) { concurrent_solves().fetch_add(k); }
+    ~Active() { concurrent_solves().fetch_sub(k); }
+  } active(nw);
   for (int w = 0; w < nw; ++w) {
     pool.emplace_back([&]() {
       cudaSetDevice(dev);
@@ -631,12 +642,12 @@ extern "C" tt_status tt_sdp_solve_batch(int32_t n, tt_sdp_ctx* const* ctxs, int3
         ctxs[i]->stream = s;
         const auto t0 = std::chrono::steady_clock::now();
         st[i] = tt_sdp_solve(ctxs[i], &out[i]);
-        cudaStreamSynchronize(s);
+        sync_stream(s);
         out[i].seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         ctxs[i]->stream = own;
       }
       if (have_stream) {
-        cudaStreamSynchronize(s);
+        sync_stream(s);
         cudaStreamDestroy(s);
       }
     });

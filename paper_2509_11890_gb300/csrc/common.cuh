@@ -94,6 +94,38 @@ inline void count_launch() { LaunchCounter::value().fetch_add(1, std::memory_ord
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Number of solves running concurrently in this process (tt_sdp_solve_batch
+// workers). With more than one, host threads that wait for their stream sleep
+// on a blocking-sync event instead of spinning: spinning waiters occupy host
+// cores that the other solves need to launch their kernels.
+inline std::atomic<int>& concurrent_solves() {
+  static std::atomic<int> n{0};
+  return n;
+}
+
+// Waits until all work queued on st has finished (cudaStreamSynchronize
+// semantics).
+inline cudaError_t sync_stream(cudaStream_t st) {
+  if (concurrent_solves().load(std::memory_order_relaxed) <= 1) return cudaStreamSynchronize(st);
+  struct Holder {
+    cudaEvent_t ev = nullptr;
+    ~Holder() {
+      if (ev) cudaEventDestroy(ev);
+    }
+  };
+  static thread_local Holder h;
+  if (!h.ev) {
+    cudaError_t e = cudaEventCreateWithFlags(&h.ev, cudaEventBlockingSync | cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      h.ev = nullptr;
+      return e;
+    }
+  }
+  cudaError_t e = cudaEventRecord(h.ev, st);
+  if (e != cudaSuccess) return e;
+  return cudaEventSynchronize(h.ev);
+}
+
 // Phase timer for diagnosing where an iteration spends its time. Enabled by
 // the environment variable TTSDP_PROFILE=1; then each scope synchronises the
 // current stream on entry and exit and accumulates host wall time per name.
@@ -132,13 +164,13 @@ struct ProfScope {
   }
   explicit ProfScope(const char* n) : name(n) {
     if (Profiler::enabled()) {
-      cudaStreamSynchronize(cur_stream());
+      sync_stream(cur_stream());
       t0 = now();
     }
   }
   ~ProfScope() {
     if (Profiler::enabled()) {
-      cudaStreamSynchronize(cur_stream());
+      sync_stream(cur_stream());
       Profiler::add(name, now() - t0);
     }
   }

@@ -117,12 +117,12 @@ RankPredictor::RankPredictor(uint64_t seed) : p_(kPredParams), m_(kPredParams), 
 
 void RankPredictor::set_params(const float* host) {
   TT_CUDA(cudaMemcpyAsync(p_.get(), host, kPredParams * sizeof(float), cudaMemcpyHostToDevice, cur_stream()));
-  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  TT_CUDA(sync_stream(cur_stream()));
 }
 
 void RankPredictor::get_params(float* host) const {
   TT_CUDA(cudaMemcpyAsync(host, p_.get(), kPredParams * sizeof(float), cudaMemcpyDeviceToHost, cur_stream()));
-  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  TT_CUDA(sync_stream(cur_stream()));
 }
 
 void RankPredictor::predict_dev(const float* X, int n, float* y) const {
@@ -148,7 +148,7 @@ std::vector<float> RankPredictor::predict(const std::vector<float>& Xh, int n) c
   predict_dev(X.get(), n, y.get());
   std::vector<float> out(n);
   TT_CUDA(cudaMemcpyAsync(out.data(), y.get(), n * sizeof(float), cudaMemcpyDeviceToHost, cur_stream()));
-  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  TT_CUDA(sync_stream(cur_stream()));
   return out;
 }
 
@@ -191,7 +191,7 @@ float RankPredictor::loss_grad_dev(const float* X, const float* t, int n, float*
   count_launch();
   float h = 0.f;
   TT_CUDA(cudaMemcpyAsync(&h, s.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
-  TT_CUDA(cudaStreamSynchronize(st));
+  TT_CUDA(sync_stream(st));
   return h / n;
 }
 
@@ -203,7 +203,7 @@ float RankPredictor::grad(const float* Xh, const float* th, int n, float* gh) {
   TT_CUDA(cudaMemcpyAsync(t.get(), th, n * sizeof(float), cudaMemcpyHostToDevice, st));
   float loss = loss_grad_dev(X.get(), t.get(), n, g.get());
   TT_CUDA(cudaMemcpyAsync(gh, g.get(), kPredParams * sizeof(float), cudaMemcpyDeviceToHost, st));
-  TT_CUDA(cudaStreamSynchronize(st));
+  TT_CUDA(sync_stream(st));
   return loss;
 }
 

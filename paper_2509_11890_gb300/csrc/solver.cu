@@ -30,8 +30,10 @@ namespace {
 // jobs have ended and their streams are drained.
 void run_concurrently(std::vector<std::function<void()>>& jobs, std::vector<cudaStream_t>& side) {
   if (jobs.empty()) return;
-  if (jobs.size() == 1) {
-    jobs[0]();
+  if (jobs.size() == 1 || concurrent_solves().load() > 1) {
+    // one job, or solves already run concurrently (more host threads would
+    // only compete with theirs for the cores): in order, on this thread
+    for (auto& j : jobs) j();
     return;
   }
   cudaStream_t main = cur_stream();
@@ -61,7 +63,7 @@ void run_concurrently(std::vector<std::function<void()>>& jobs, std::vector<cuda
         TT_CUDA(cudaEventRecord(done[i], s));
       } catch (...) {
         err[i] = std::current_exception();
-        cudaStreamSynchronize(s);
+        sync_stream(s);
       }
     });
   }
@@ -169,13 +171,13 @@ double dev_norm(const double* p, size_t n) { return std::sqrt(std::max(0.0, dev_
 std::vector<double> host_copy(const double* p, size_t n) {
   std::vector<double> h(n);
   TT_CUDA(cudaMemcpyAsync(h.data(), p, n * sizeof(double), cudaMemcpyDeviceToHost, cur_stream()));
-  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  TT_CUDA(sync_stream(cur_stream()));
   return h;
 }
 
 void upload(double* dst, const std::vector<double>& h) {
   TT_CUDA(cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, cur_stream()));
-  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  TT_CUDA(sync_stream(cur_stream()));
 }
 
 int truncation_rank_rel(const std::vector<double>& s, double tol_rel, int cap) {
@@ -206,8 +208,6 @@ void svd_prec(int prec, MatView<double> A, double* U, double* S, double* Vt, cud
   if (side != kSvdLeft) to_f64(vt.get(), Vt, (size_t)k * n, st);
 }
 
-// Dense local solve K x = b (K destroyed, b becomes x). The mixed precisions
-// factor in FP32 and refine the solution twice against the FP64 residual.
 // FP64 relative residual at which the refinement of a dense local solve stops
 // (the accuracy of an FP64 LU of the projected system)
 constexpr double kLuRefineTol = 1e-10;
@@ -323,7 +323,7 @@ int gmres(size_t N, const std::function<void(const double*, double*)>& A, const 
         dev_multi_dot(V.get(), j + 1, N, w.get(), hdev.get(), st);
         std::vector<double> h(j + 1);
         TT_CUDA(cudaMemcpyAsync(h.data(), hdev.get(), (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-        TT_CUDA(cudaStreamSynchronize(st));
+        TT_CUDA(sync_stream(st));
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
         gemm_rm<double>(true, false, (int)N, 1, j + 1, -1.0, V.get(), (int)N, 0, hdev.get(), 1, 0, 1.0, w.get(), 1, 0,
                         1, st);
@@ -799,7 +799,7 @@ static double local_min_eig(int nl, const double* Mk, const double* Dk, double* 
   cholesky_lower<double>(nl, L.get(), st, nonpos.get());
   int h_nonpos = 0;
   TT_CUDA(cudaMemcpyAsync(&h_nonpos, nonpos.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
-  TT_CUDA(cudaStreamSynchronize(st));
+  TT_CUDA(sync_stream(st));
   // Section 3.4: an iterate that is not positive definite shows in its
   // projection; the step length is then undefined and the error is raised
   TT_CHECK(!h_nonpos, TT_E_NOT_PD, "step length: the projected iterate is not positive definite");
@@ -1177,7 +1177,7 @@ void Solver::set_deadline(double seconds_from_now) {
 
 Solver::~Solver() {
   for (cudaStream_t s : side_) {
-    cudaStreamSynchronize(s);
+    sync_stream(s);
     cudaStreamDestroy(s);
   }
 }

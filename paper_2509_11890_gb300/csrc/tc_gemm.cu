@@ -375,11 +375,11 @@ int tc_check_error(bool reset) {
   cudaStream_t st = cur_stream();
   int h = 0;
   TT_CUDA(cudaMemcpyFromSymbolAsync(&h, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
-  TT_CUDA(cudaStreamSynchronize(st));
+  TT_CUDA(sync_stream(st));
   if (reset && h) {
     int z = 0;
     TT_CUDA(cudaMemcpyToSymbolAsync(g_tc_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st));
-    TT_CUDA(cudaStreamSynchronize(st));
+    TT_CUDA(sync_stream(st));
   }
   return h;
 }

@@ -262,7 +262,7 @@ double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st) {
   check_launch("dot");
   double h = 0.0;
   TT_CUDA(cudaMemcpyAsync(&h, out.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
-  TT_CUDA(cudaStreamSynchronize(st));
+  TT_CUDA(sync_stream(st));
   return h;
 }
 
@@ -308,7 +308,7 @@ void tt_to_host(const DTT& a, double* out) {
                             cur_stream()));
     off += a.csize(k);
   }
-  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  TT_CUDA(sync_stream(cur_stream()));
 }
 
 void tt_to_device(const DTT& a, double* out) {
@@ -454,7 +454,7 @@ DTT tt_identity(int d, int m) {
   for (int i = 0; i < m; ++i) h[(size_t)i * m + i] = 1.0;
   for (int k = 0; k < d; ++k)
     TT_CUDA(cudaMemcpyAsync(t.core(k), h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, cur_stream()));
-  TT_CUDA(cudaStreamSynchronize(cur_stream()));
+  TT_CUDA(sync_stream(cur_stream()));
   return t;
 }
 
@@ -500,7 +500,7 @@ double tt_inner(const DTT& a, const DTT& b) {
   }
   double h = 0.0;
   TT_CUDA(cudaMemcpyAsync(&h, phi.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
-  TT_CUDA(cudaStreamSynchronize(st));
+  TT_CUDA(sync_stream(st));
   return h;
 }
 
@@ -562,7 +562,7 @@ DTT tt_from_dense(const double* dense, int d, int n, double eps_rel, int cap) {
     svd_thin<double>(MatView<double>{cur->get(), rows, (int)cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
     std::vector<double> hs(kk);
     TT_CUDA(cudaMemcpyAsync(hs.data(), S.get(), kk * sizeof(double), cudaMemcpyDeviceToHost, st));
-    TT_CUDA(cudaStreamSynchronize(st));
+    TT_CUDA(sync_stream(st));
     const int keep = truncation_rank(hs, thr, cap);
     cores[k] = std::make_shared<DBuf<double>>((size_t)rows * keep);
     dev_copy2d(cores[k]->get(), keep, U.get(), kk, rows, keep, 1.0, st);
@@ -624,7 +624,7 @@ static int round_bond_sketch(DTT& t, int k, int l, double thr, int cap, Counter&
   {
     std::vector<double> h = rnd.draw((size_t)l * r2);
     TT_CUDA(cudaMemcpyAsync(Om.get(), h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    TT_CUDA(cudaStreamSynchronize(st));
+    TT_CUDA(sync_stream(st));
   }
   tc_gemm_f64_tn(rows, l, r2, A, r2, Om.get(), r2, Y.get(), st);  // Y = A Omega, Omega^T stored l x r2
   qr_thin<double>(MatView<double>{Y.get(), rows, l, l, 1}, Q.get(), Rq.get(), st);
@@ -712,7 +712,7 @@ std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* 
     }
     std::vector<double> hs(kk);
     TT_CUDA(cudaMemcpyAsync(hs.data(), S.get(), kk * sizeof(double), cudaMemcpyDeviceToHost, st));
-    TT_CUDA(cudaStreamSynchronize(st));
+    TT_CUDA(sync_stream(st));
     int keep = truncation_rank(hs, thr, cap);
     for (int j = keep; j < kk; ++j) zeta2 += hs[j] * hs[j];
     if (hook && hook->trace_x && !feats.empty()) {  // the adaptive SVD's choice is the label
