@@ -249,6 +249,29 @@ def _run_reference_batch(a, w):
     return 0
 
 
+def _cpu_baseline_batch(insts, count=8):
+    """The oracle's TT-IPM (O4, numpy FP64) on the host cores, one instance after
+    another, on a bounded sample: the first `count` instances of the batch's
+    smallest order (larger orders can take minutes each in numpy); instances/s
+    over the sample."""
+    from oracle import tt_ipm, tt_problems as tp
+    t_all, n, nconv, per = 0.0, 0, 0, []
+    dmin = min(i["d"] for i in insts)
+    for i in [x for x in insts if x["d"] == dmin][:count]:
+        ipm = tt_ipm.TTIPM(tp.maxcut(i["adjacency_cores"], i["d"]), tt_ipm.Options(rank_cap=64, max_iters=40))
+        t0 = time.perf_counter()
+        ok = ipm.solve()
+        dt = time.perf_counter() - t0
+        t_all += dt
+        per.append(dt)
+        n += 1
+        nconv += int(ok)
+    return {"value": n / t_all if t_all > 0 else None, "unit": "instances/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"TT-IPM oracle O4 (numpy FP64) on the first {n} instances of order d = {dmin} of the batch, "
+                      f"one after another ({nconv} certified, {t_all:.1f} s, p50 {float(np.median(per)):.2f} s)"}
+
+
 def _cpu_baseline(w, seed, budget_s=30.0):
     """Oracle O2 time-to-gap on the same instance (bounded: one solve, ~10-30 s of CPU work)."""
     from oracle import sdp_dense as sd
@@ -474,6 +497,8 @@ def run_batch(a):
                 "note": "contexts are created from host cores before the timed region; the step reads back "
                         "one result record per instance"},
     }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = _cpu_baseline_batch(insts)
     if rank == 0 and a.sequential > 0:
         # one at a time in the plain FP64 form, on a bounded sample of the batch
         o64 = tg.default_options(rank_cap=w["cap"], precision=0, max_iters=60, time_limit=a.time_limit)
