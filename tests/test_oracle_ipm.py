@@ -225,3 +225,17 @@ def test_damp_and_retry_repairs_an_update_that_left_the_cone():
     assert np.linalg.eigvalsh(tt.full_mat(ipm.X))[0] > 0
     h = ipm.history[-1]
     assert abs(h.pobj - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3
+
+
+def test_warm_start_frame_stays_within_the_rank_cap():
+    # the solution is read where the last sweep ended; the warm start moved
+    # back to core 0 is truncated like the sweeps' moves, so its frame keeps
+    # the cap (an exact move would grow it to nblk times the rank)
+    d, seed, cap = 5, 1, 4
+    inst, prob = _maxcut(d, seed)
+    # one sweep per solve: every sweep ends at core d-1, so every warm start is moved
+    ipm = tt_ipm.TTIPM(prob, tt_ipm.Options(rank_cap=cap, max_iters=10, max_sweeps=1, kick=4))
+    for it in range(3):
+        ipm.iterate(it)
+        assert ipm.w.pos == 0
+        assert max(tt.ranks(ipm.w.cores)) <= cap, tt.ranks(ipm.w.cores)
