@@ -50,7 +50,10 @@ typedef enum {
   TT_E_INTERNAL = 10
 } tt_status;
 
-/* Arithmetic used by the contractions (environments, local products). */
+/* Arithmetic used by the contractions (environments, local products). In the
+ * three reduced precisions every AMEn solve closes with one FP64 sweep
+ * (FP64 environments, local operators and solves) that refines the direction,
+ * and rounding, residuals, norms and step lengths stay FP64. */
 typedef enum {
   TT_FP64 = 0,        /* everything in FP64                                          */
   TT_FP32 = 1,        /* FP32 SIMT contractions, FP32 accumulation                   */
@@ -216,7 +219,8 @@ typedef struct {
   double damping;      /* step damping factor (0.95)                                   */
   int32_t precision;   /* tt_precision of the contractions                             */
   int32_t max_iters;
-  int32_t max_sweeps;  /* AMEn sweeps per Newton solve                                 */
+  int32_t max_sweeps;  /* AMEn sweeps per Newton solve (reduced precisions: plus the
+                          closing FP64 sweep)                                        */
   int32_t kick;        /* AMEn random enrichment columns                               */
   int32_t eig_rank;    /* TT rank of the step-length eigenvector                       */
   int32_t eig_sweeps;
