@@ -334,7 +334,7 @@ void tt_sdp_destroy(tt_sdp_ctx* ctx);
  * sketch product runs on the TF32 tensor cores. The exact FP64 truncation
  * error of the sketched bond is checked against the bond tolerance; when it
  * exceeds it (or the rank cap would bind) the bond falls back to the
- * adaptive SVD, which stays the judge. Network: 9 features -> 64 -> 64 -> 64
+ * adaptive SVD, which has the final word. Network: 9 features -> 64 -> 64 -> 64
  * -> 1, tanh hidden layers, sigmoid output = rank / cap, trained on the GPU
  * (mean squared error, Adam) by the library's own kernels. Features of a
  * bond: one-hot variable (X, Y, T, Z), bond position k/(d-2), log10(mu)/10,
