@@ -24,6 +24,14 @@ convention of Section 2.3):
   N(N-1)/2) seeded pairs u < v have their sign flipped (mirrored).
 * ``batch_maxcut``: many Kronecker Max-Cut instances with d drawn uniformly
   from a range.
+* ``rank_controlled_graph``: the paper's instance family with a prescribed
+  input TT rank r (Appendix A): a state in {0..r-1} is carried digit by digit;
+  the first digit pair picks a state, every middle digit pair maps states to
+  states (or drops them), the last digit pair names the state that makes the
+  entry 1. Every choice is the same for the digit pairs (a, b) and (b, a), so
+  the graph is undirected; on the middle digits' diagonal pairs (a, a) the
+  states that diagonal paths can hold are dropped, so there are no loops.
+  Draws whose TT rank is not exactly r, or without edges, are rejected.
 
 Random streams come from numpy's Philox counter-based generator keyed by
 (seed, stream id), so every workload is reproducible from its seed alone.
@@ -38,6 +46,7 @@ __all__ = [
     "kron_dense",
     "kron_adjacency_cores",
     "maxcut_kron",
+    "rank_controlled_graph",
     "maxcut_kron_er",
     "theta_hypercube_kron",
     "cc_signed",
@@ -55,6 +64,7 @@ _STREAM_CC = 5
 _STREAM_CC_FLIP = 6
 _STREAM_BATCH = 7
 _STREAM_TT = 8
+_STREAM_APPA = 9
 
 
 def rng(seed: int, stream: int = 0) -> np.random.Generator:
@@ -256,3 +266,90 @@ def batch_maxcut(count: int, seed: int, d_lo: int = 6, d_hi: int = 11) -> list[d
     g = rng(seed, _STREAM_BATCH)
     ds = g.integers(d_lo, d_hi + 1, size=count)
     return [maxcut_kron(int(dd), seed * 100003 + i) for i, dd in enumerate(ds)]
+
+
+def _tt_unfolding_ranks(adj: np.ndarray, d: int) -> list[int]:
+    """Ranks of the unfoldings of the 2 x 2-mode TT matrix of adj (bond k splits
+    the digit pairs 1..k from k+1..d), from the plain definition."""
+    t = adj.reshape([2] * d + [2] * d)
+    # interleave (row digit k, column digit k)
+    order = [x for k in range(d) for x in (k, d + k)]
+    t = np.transpose(t, order)
+    out = []
+    for k in range(1, d):
+        out.append(int(np.linalg.matrix_rank(t.reshape(4 ** k, 4 ** (d - k)).astype(np.float64))))
+    return out
+
+
+def rank_controlled_graph(d: int, r: int, seed: int, stay: float = 0.5, max_draws: int = 500) -> dict:
+    """Undirected graph without loops on 2**d vertices whose adjacency has TT
+    rank exactly r (2 x 2 modes), drawn by the construction described in the
+    module docstring. `stay` is the probability that a middle digit pair keeps
+    a state unchanged (larger: denser graphs). Also returns the exact TT
+    cores (bond dimension r) of the adjacency."""
+    assert d >= 3 and r >= 1
+    g = rng(seed, _STREAM_APPA)
+    n = 2 ** d
+    pairs = [(0, 0), (0, 1), (1, 1)]
+    for _ in range(max_draws):
+        first = np.zeros((2, 2), dtype=np.int64)
+        last = np.zeros((2, 2), dtype=np.int64)
+        maps = np.zeros((d - 2, 2, 2, r), dtype=np.int64)  # -1: the state is dropped
+        for a, b in pairs:
+            first[a, b] = first[b, a] = g.integers(r)
+        reach = {int(first[0, 0]), int(first[1, 1])}  # states of diagonal paths
+        for k in range(d - 2):
+            for a, b in pairs:
+                m = np.where(g.random(r) < stay, np.arange(r), g.integers(r, size=r))
+                if a == b:
+                    m[list(reach)] = -1
+                maps[k, a, b] = maps[k, b, a] = m
+            reach = set()  # every diagonal path is dropped at the first middle digit
+        for a, b in pairs:
+            last[a, b] = last[b, a] = g.integers(r)
+        # entry (u, v): carry the state through the digits of u and v
+        digits = (np.arange(n)[:, None] >> np.arange(d - 1, -1, -1)[None, :]) & 1  # (n, d), digit 1 first
+        du = digits[:, None, :]
+        dv = digits[None, :, :]
+        state = np.broadcast_to(first[du[..., 0], dv[..., 0]], (n, n)).copy()
+        for k in range(d - 2):
+            mk = maps[k][du[..., k + 1], dv[..., k + 1]]  # (n, n, r)
+            alive = state >= 0
+            nxt = np.full_like(state, -1)
+            idx = np.where(alive)
+            nxt[idx] = mk[idx[0], idx[1], state[idx]]
+            state = nxt
+        adj = (state == last[du[..., d - 1], dv[..., d - 1]]).astype(np.int8)
+        if adj.sum() == 0 or np.any(np.diag(adj)) or max(_tt_unfolding_ranks(adj, d)) != r:
+            continue
+        # exact TT cores (1 x 2 x 2 x r, r x 2 x 2 x r, r x 2 x 2 x 1)
+        cores = []
+        c = np.zeros((1, 2, 2, r))
+        for a in range(2):
+            for b in range(2):
+                c[0, a, b, first[a, b]] = 1.0
+        cores.append(c)
+        for k in range(d - 2):
+            c = np.zeros((r, 2, 2, r))
+            for a in range(2):
+                for b in range(2):
+                    for i in range(r):
+                        if maps[k, a, b, i] >= 0:
+                            c[i, a, b, maps[k, a, b, i]] = 1.0
+            cores.append(c)
+        c = np.zeros((r, 2, 2, 1))
+        for a in range(2):
+            for b in range(2):
+                c[last[a, b], a, b, 0] = 1.0
+        cores.append(c)
+        return {
+            "kind": "maxcut",
+            "d": d,
+            "seed": seed,
+            "r_in": r,
+            "adjacency": adj,
+            "weights": adj.astype(np.float64),
+            "adjacency_cores": cores,
+        }
+    raise RuntimeError(f"no graph of TT rank {r} at d = {d} in {max_draws} draws")
+

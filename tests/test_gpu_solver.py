@@ -144,3 +144,14 @@ def test_time_limit_stops_a_solve_and_keeps_the_last_iterate():
     ctx2 = tg.Context.maxcut(inst["adjacency_cores"], _opts())
     res2 = ctx2.solve()
     assert res2["status"] == 0 and abs(res2["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3
+
+
+@pytest.mark.parametrize("d,r,seed", [(5, 2, 5), (6, 3, 6)])
+def test_rank_controlled_maxcut_reaches_dense_optimum(d, r, seed):
+    # the paper's instance family (Appendix A) with input TT rank r
+    inst = inputs.rank_controlled_graph(d, r, seed)
+    ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]))
+    ctx = tg.Context.maxcut(inst["adjacency_cores"], _opts(rank_cap=32))
+    res = ctx.solve()
+    assert res["status"] == 0, res
+    assert abs(res["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 2e-3
