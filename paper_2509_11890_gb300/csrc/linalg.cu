@@ -6,6 +6,10 @@
 // local systems is blocked so that its trailing updates use the multi-CTA
 // strided GEMM.
 #include <cfloat>
+#include <cmath>
+#include <vector>
+#include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -533,6 +537,68 @@ __global__ void newton_schulz_rhs_kernel(double* G, int n) {
   }
 }
 
+// One step of the first-order Jacobi finish on the Gram matrix G = W^T W of
+// nearly orthogonal columns: J = I + K with K_ij = G_ij / (G_jj - G_ii) for
+// the pairs that are not yet orthogonal to working precision (the skew K that
+// makes J^T G J diagonal to first order); *maxbits receives max |K_ij| as the
+// bits of a non-negative double (monotone in the value), infinity when a pair
+// is not orthogonal but its diagonal entries are equal.
+__global__ void first_order_rotation_kernel(const double* G, int n, double tol, double floor2, double* J,
+                                            unsigned long long* maxbits) {
+  const long long tot = (long long)n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    double v = 0.0;
+    if (i == j) {
+      v = 1.0;
+    } else {
+      const double gii = G[(long long)i * n + i], gjj = G[(long long)j * n + j];
+      const double gij = 0.5 * (G[(long long)i * n + j] + G[(long long)j * n + i]);
+      const bool orth = (gii <= floor2 && gjj <= floor2) || fabs(gij) <= tol * sqrt(fabs(gii * gjj));
+      if (!orth) {
+        const double den = gjj - gii;
+        v = den != 0.0 ? gij / den : HUGE_VAL;
+        atomicMax(maxbits, (unsigned long long)__double_as_longlong(fabs(v)));
+      }
+      if (!isfinite(v)) v = 0.0;
+    }
+    J[e] = v;
+  }
+}
+
+// norms[j] = || column j of W (m x n, row-major) ||
+__global__ void column_norms_kernel(const double* W, int m, int n, double* norms) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < m; ++i) a += W[(long long)i * n + j] * W[(long long)i * n + j];
+    norms[j] = sqrt(a);
+  }
+}
+
+// SVD factors from orthogonal columns W = B V (B m x n): S descending by perm,
+// the W side (U of B, or Vt of A = B^T when transposed) always, the V side
+// when need_v, in the layouts svd_thin returns.
+__global__ void finish_svd_kernel(const double* W, const double* V, const double* norms, const int* perm, int m,
+                                  int n, bool transposed, bool need_v, double* U, double* S, double* Vt) {
+  const long long totw = (long long)m * n, totv = (long long)n * n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < totw; e += stride) {
+    const int i = (int)(e / n), r = (int)(e % n);
+    const int c = perm[r];
+    const double s = norms[c];
+    const double val = s > 0.0 ? W[(long long)i * n + c] / s : 0.0;
+    if (!transposed) U[(long long)i * n + r] = val;   // U (m x k)
+    else Vt[(long long)r * m + i] = val;               // Vt (k x m)
+  }
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; need_v && e < totv; e += stride) {
+    const int j = (int)(e / n), r = (int)(e % n);
+    const double val = V[(long long)j * n + perm[r]];
+    if (!transposed) Vt[(long long)r * n + j] = val;  // Vt (k x n)
+    else U[(long long)j * n + r] = val;               // U (n x k)
+  }
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) S[e] = norms[perm[e]];
+}
+
 int grid_for(long long n) {
   long long g = (n + 255) / 256;
   if (g < 1) g = 1;
@@ -552,6 +618,81 @@ void qr_thin(MatView<T> A, T* Q, T* R, cudaStream_t st) {
   qr_kernel<T><<<1, kThreads, 0, st>>>(A, W.get(), tau.get(), Q, R);
   count_launch();
   check_launch("qr_kernel");
+}
+
+// Finishes the SVD of B from W = B V (V orthonormal, W's columns nearly
+// orthogonal) by first-order Jacobi steps computed from the Gram matrix with
+// multi-CTA GEMMs: each step rotates by J = orth(I + K) (K from
+// first_order_rotation_kernel, one Newton-Schulz step), which squares the
+// remaining angles, until every pair is orthogonal to working precision (the
+// tolerance of the one-CTA Jacobi kernel). W and V are updated in place.
+// Returns false, leaving the sweeps to the Jacobi kernel, when an angle is
+// not small (clustered or equal singular values) or three steps do not
+// converge.
+bool first_order_finish(DBuf<double>& W, DBuf<double>& V, int m, int n, bool transposed, bool need_v, double* U,
+                        double* S, double* Vt, cudaStream_t st) {
+  constexpr double kMaxAngle = 1e-3;  // first-order steps only from here down
+  DBuf<double> G((size_t)n * n), J((size_t)n * n), H((size_t)n * n), W2((size_t)m * n), V2((size_t)n * n);
+  DBuf<unsigned long long> maxbits(1);
+  const double tol = 4.0 * std::sqrt((double)m) * DBL_EPSILON;
+  // the noise floor of the one-CTA kernel: (sqrt(m) eps ||B||_F)^2
+  double fro2 = 0.0;
+  {
+    DBuf<double> nrm((size_t)n);
+    column_norms_kernel<<<ceil_div(n, 128), 128, 0, st>>>(W.get(), m, n, nrm.get());
+    count_launch();
+    std::vector<double> h((size_t)n);
+    TT_CUDA(cudaMemcpyAsync(h.data(), nrm.get(), n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(sync_stream(st));
+    for (double v : h) fro2 += v * v;
+  }
+  const double floor2 = (double)m * DBL_EPSILON * DBL_EPSILON * fro2;
+  bool converged = false;
+  for (int step = 0; step < 3; ++step) {
+    gemm_rm<double>(true, false, n, n, m, 1.0, W.get(), n, 0, W.get(), n, 0, 0.0, G.get(), n, 0, 1, st);
+    TT_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
+    first_order_rotation_kernel<<<grid_for((long long)n * n), 256, 0, st>>>(G.get(), n, tol, floor2, J.get(),
+                                                                            maxbits.get());
+    count_launch();
+    unsigned long long hb = 0;
+    TT_CUDA(cudaMemcpyAsync(&hb, maxbits.get(), sizeof(hb), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(sync_stream(st));
+    double maxang = 0.0;
+    std::memcpy(&maxang, &hb, sizeof(double));
+    if (hb == 0) {
+      converged = true;
+      break;
+    }
+    if (!(maxang <= kMaxAngle)) return false;
+    // J <- J (3 I - J^T J) / 2, then W <- W J, V <- V J
+    gemm_rm<double>(true, false, n, n, n, 1.0, J.get(), n, 0, J.get(), n, 0, 0.0, G.get(), n, 0, 1, st);
+    newton_schulz_rhs_kernel<<<grid_for((long long)n * n), 256, 0, st>>>(G.get(), n);
+    count_launch();
+    gemm_rm<double>(false, false, n, n, n, 1.0, J.get(), n, 0, G.get(), n, 0, 0.0, H.get(), n, 0, 1, st);
+    gemm_rm<double>(false, false, m, n, n, 1.0, W.get(), n, 0, H.get(), n, 0, 0.0, W2.get(), n, 0, 1, st);
+    gemm_rm<double>(false, false, n, n, n, 1.0, V.get(), n, 0, H.get(), n, 0, 0.0, V2.get(), n, 0, 1, st);
+    std::swap(W, W2);
+    std::swap(V, V2);
+  }
+  if (!converged) return false;
+  // singular values, a stable descending order, the factors
+  DBuf<double> norms((size_t)n);
+  column_norms_kernel<<<ceil_div(n, 128), 128, 0, st>>>(W.get(), m, n, norms.get());
+  count_launch();
+  std::vector<double> hs((size_t)n);
+  TT_CUDA(cudaMemcpyAsync(hs.data(), norms.get(), n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(sync_stream(st));
+  std::vector<int> perm((size_t)n);
+  for (int j = 0; j < n; ++j) perm[(size_t)j] = j;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return hs[(size_t)a] > hs[(size_t)b]; });
+  DBuf<int> dperm((size_t)n);
+  TT_CUDA(cudaMemcpyAsync(dperm.get(), perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+  finish_svd_kernel<<<grid_for((long long)m * n), 256, 0, st>>>(W.get(), V.get(), norms.get(), dperm.get(), m, n,
+                                                                transposed, need_v, U, S, Vt);
+  count_launch();
+  check_launch("first-order svd finish");
+  TT_CUDA(sync_stream(st));  // perm (host memory) is read by the copy above
+  return true;
 }
 
 template <typename T>
@@ -620,6 +761,7 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st, SvdSide side) {
       gemm_rm<double>(false, false, n, n, n, 1.0, H.get(), n, 0, G.get(), n, 0, 0.0, V0.get(), n, 0, 1, st);
       gemm_rm<double>(false, false, m, n, n, 1.0, B64.get(), n, 0, V0.get(), n, 0, 0.0, W.get(), n, 0, 1, st);
       check_launch("svd preconditioning");
+      if (first_order_finish(W, V0, m, n, tr, need_v, U, S, Vt, st)) return;
       MatView<double> wv{W.get(), m, n, n, 1};
       if (!tr) {
         svd_kernel<double><<<1, kThreads, smem, st>>>(wv, false, Wc.get(), Vc.get(), w_smem, v_smem, U, S, Vt,
