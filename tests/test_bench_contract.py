@@ -35,3 +35,27 @@ def test_batch_partition_covers_every_order_of_the_batch():
     assert {i["d"] for i in insts} == set(range(6, 12))
     shards = bench.partition_batch([i["d"] for i in insts], 4, 64)
     assert all(len(sh) > 0 for sh in shards)
+
+
+def test_clock_summary_reads_throttle_reasons_and_median_clock():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.Clocks(0)
+    # index, sm, max sm, power, active, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    c.rows = [["0", "2070", "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+              ["0", "2010", "2070", "1390", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+              ["0", "2070", "2070", "950", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+    assert bench.Clocks(0).summary()["reasons"] == ["unsampled"]
+
+
+def test_single_process_helpers():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.replica_seed(5, 0) == 5 and bench.replica_seed(5, 3) == 8
+    assert bench.max_over_ranks([1.5, 2.5]) == [1.5, 2.5]          # no process group: identity
+    assert bench.gather_results({3: (0, 1.0, 4)}, 1) == {3: (0, 1.0, 4)}
+    assert set(bench.WORKLOADS) >= {"maxcut_d10_kron_er_cap64", "maxcut_d6_kron_cap16",
+                                     "maxcut_batch64_d6to11_cap64"}
