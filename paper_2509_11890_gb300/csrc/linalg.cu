@@ -599,6 +599,16 @@ __global__ void finish_svd_kernel(const double* W, const double* V, const double
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) S[e] = norms[perm[e]];
 }
 
+// *maxbits <- max |G_ij - delta_ij| as the bits of a non-negative double
+__global__ void max_offset_from_identity_kernel(const double* G, int n, unsigned long long* maxbits) {
+  const long long tot = (long long)n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const double v = fabs(G[e] - (i == j ? 1.0 : 0.0));
+    atomicMax(maxbits, (unsigned long long)__double_as_longlong(isfinite(v) ? v : HUGE_VAL));
+  }
+}
+
 int grid_for(long long n) {
   long long g = (n + 255) / 256;
   if (g < 1) g = 1;
@@ -610,9 +620,56 @@ constexpr int kPrecondMinCols = 16;
 
 }  // namespace
 
+// FP64 tall-skinny QR by CholeskyQR2 on all SMs: twice G = A^T A (GEMM),
+// G = L L^T (one CTA, n x n), Q = A L^-T (GEMM), R = R2 R1. Returns false,
+// leaving Q and R to the Householder kernel, when a Cholesky pivot is not
+// positive (rank deficiency at working precision) or Q^T Q is not the
+// identity to 1e-12 (condition number beyond what two passes repair).
+bool cholesky_qr2(MatView<double> A, double* Q, double* R, cudaStream_t st) {
+  const int m = A.m, n = A.n;
+  DBuf<double> A64((size_t)m * n), Q1((size_t)m * n), G((size_t)n * n), L((size_t)n * n), R1((size_t)n * n),
+      R2((size_t)n * n);
+  DBuf<int> nonpos(1);
+  DBuf<unsigned long long> maxbits(1);
+  transpose_view_kernel<double><<<grid_for((long long)m * n), 256, 0, st>>>(A.p, A.cs, A.rs, m, n, A64.get());
+  count_launch();
+  auto pass = [&](const double* Ain, double* Qout, double* Rout) -> bool {
+    gemm_rm<double>(true, false, n, n, m, 1.0, Ain, n, 0, Ain, n, 0, 0.0, G.get(), n, 0, 1, st);
+    TT_CUDA(cudaMemcpyAsync(L.get(), G.get(), sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
+    TT_CUDA(cudaMemsetAsync(nonpos.get(), 0, sizeof(int), st));
+    cholesky_lower<double>(n, L.get(), st, nonpos.get());
+    int h = 0;
+    TT_CUDA(cudaMemcpyAsync(&h, nonpos.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(sync_stream(st));
+    if (h) return false;
+    transpose<double>(n, n, L.get(), Rout, st);   // R = L^T
+    tri_lower_inverse<double>(n, L.get(), st);     // L <- L^-1
+    gemm_rm<double>(false, true, m, n, n, 1.0, Ain, n, 0, L.get(), n, 0, 0.0, Qout, n, 0, 1, st);
+    return true;
+  };
+  if (!pass(A64.get(), Q1.get(), R1.get())) return false;
+  if (!pass(Q1.get(), Q, R2.get())) return false;
+  gemm_rm<double>(true, false, n, n, m, 1.0, Q, n, 0, Q, n, 0, 0.0, G.get(), n, 0, 1, st);
+  TT_CUDA(cudaMemsetAsync(maxbits.get(), 0, sizeof(unsigned long long), st));
+  max_offset_from_identity_kernel<<<grid_for((long long)n * n), 256, 0, st>>>(G.get(), n, maxbits.get());
+  count_launch();
+  unsigned long long hb = 0;
+  TT_CUDA(cudaMemcpyAsync(&hb, maxbits.get(), sizeof(hb), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(sync_stream(st));
+  double off = 0.0;
+  std::memcpy(&off, &hb, sizeof(double));
+  if (!(off <= 1e-12)) return false;
+  gemm_rm<double>(false, false, n, n, n, 1.0, R2.get(), n, 0, R1.get(), n, 0, 0.0, R, n, 0, 1, st);
+  check_launch("cholesky_qr2");
+  return true;
+}
+
 template <typename T>
 void qr_thin(MatView<T> A, T* Q, T* R, cudaStream_t st) {
   if (A.m == 0 || A.n == 0) return;
+  if constexpr (std::is_same<T, double>::value) {
+    if (A.m >= 2 * A.n && A.n >= kPrecondMinCols && cholesky_qr2(A, Q, R, st)) return;
+  }
   int k = A.m < A.n ? A.m : A.n;
   DBuf<T> W((size_t)A.m * A.n), tau((size_t)k);
   qr_kernel<T><<<1, kThreads, 0, st>>>(A, W.get(), tau.get(), Q, R);
