@@ -277,11 +277,66 @@ typedef struct {
  * eta floor 1e-4, C = 2) and of this library (damping 0.95, kick 4, ...). */
 void tt_sdp_default_options(tt_sdp_options* opts);
 
+/* Device memory hook. Every device buffer a context allocates (iterates,
+ * environments, scratch of the sweeps) comes from `alloc` and goes back
+ * through `free`, with the CUDA stream the library works on at that moment
+ * (all earlier work that touches the block is ordered before that point on
+ * it) and the caller's `user` pointer; a framework that owns the device heap
+ * (a caching allocator) passes its own pair here. `alloc` returns NULL when
+ * it cannot satisfy the request (the call then fails with TT_E_NOMEM); sizes
+ * are bytes and blocks must be 256-byte aligned. The struct is copied at
+ * create; the functions must stay callable until the context is destroyed
+ * and may be called from library worker threads. NULL selects the device's
+ * default stream-ordered memory pool (cudaMallocAsync). The
+ * step-length and rounding calls outside a context always use the pool. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, void* stream, void* user);
+  void* user;
+} tt_allocator;
+
 /* Copies the problem to the device and sets the initial point of Section 5.1:
  * X = Z = lam0 I, Y = 0 (with inequalities X = lam0 I + (alpha_p/10) 1_T,
- * T = lam0_ineq 1_T). */
-tt_status tt_sdp_create(const tt_sdp_problem* prob, const tt_sdp_options* opts, void* stream,
-                        tt_sdp_ctx** out);
+ * T = lam0_ineq 1_T). `allocator` may be NULL (default pool). */
+tt_status tt_sdp_create(const tt_sdp_problem* prob, const tt_sdp_options* opts, const tt_allocator* allocator,
+                        void* stream, tt_sdp_ctx** out);
+
+/* A batch of n independent SDPs (the many-instance workload; each instance as
+ * for tt_sdp_create, same options). tt_sdp_solve on the returned context
+ * solves every instance concurrently (one host worker thread and one CUDA
+ * stream per concurrently running instance, at most 16) and writes n results;
+ * tt_sdp_newton_step and tt_sdp_get_iterate reject a batch context (read an
+ * instance through tt_sdp_batch_member). tt_sdp_destroy frees every
+ * instance. */
+tt_status tt_sdp_create_batch(int32_t n, const tt_sdp_problem* probs, const tt_sdp_options* opts,
+                              const tt_allocator* allocator, void* stream, tt_sdp_ctx** out);
+/* Number of instances of a batch context (1 for a single context). */
+int32_t tt_sdp_batch_size(const tt_sdp_ctx* ctx);
+/* Instance i of a batch context, owned by the batch (NULL when out of range). */
+tt_sdp_ctx* tt_sdp_batch_member(tt_sdp_ctx* ctx, int32_t i);
+
+/* Row a9 on host data: TT rounding (Section 2.3, round_TT) followed by the
+ * spectral shift of Section 3.4, Corollary psdness_rounding. `in` names HOST
+ * cores of a TT matrix (m = n) or vector (n = 1). The input is rounded as a
+ * vector (m * n per core): bond k keeps the smallest rank whose discarded
+ * energy is <= (delta / sqrt(d-1))^2, then at most rank_cap (<= 0: no cap);
+ * zeta = sqrt(sum of all discarded sigma^2) = ||in - round(in)||_F.
+ *   psd_shift 0: out = round(in) at delta = tol.
+ *   psd_shift 1: out = round(in) + zeta I (X and Z of the SDP), rounded at
+ *                delta = tol / (1 + ||I||_F) so that ||in - out||_F <= tol.
+ *   psd_shift 2: out = round(in) + zeta (J - I), the inequality mask 1_T of
+ *                the complete-graph constraints of Section 4.3 (the
+ *                multiplier T), rounded at tol / (1 + ||J - I||_F).
+ * Shifts need a square TT matrix (m = n). `out` is caller-owned: out->ranks
+ * points to a writable array of d + 1 ints that receives the ranks and
+ * out->cores to a writable host buffer (the const qualifiers of tt_desc
+ * describe inputs); out->d, m, n are set from `in`. With out->cores == NULL
+ * only the ranks are written (size query: the buffer needs
+ * tt_core_count(d, ranks, m, n) doubles); the rounding is deterministic, so a
+ * second call with the buffer writes cores of exactly those ranks.
+ * *zeta_out receives zeta. FP64 on the device; synchronises the stream. */
+tt_status tt_sdp_round(const tt_desc* in, double tol, int32_t rank_cap, int32_t psd_shift, tt_desc* out,
+                       double* zeta_out, void* stream);
 
 /* Row a1: assemble the Section 4 formulations on the device from the graph
  * adjacency given as a host TT matrix (2 x 2 modes, zero diagonal) and create
@@ -300,7 +355,18 @@ tt_status tt_sdp_create_cc(const tt_desc* c_plus, const tt_desc* c_minus, const 
  * TT_OK with info->converged = 1 when the stopping rules already hold. */
 tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info);
 
-/* Iterates until the stopping rules hold or max_iters. */
+/* Undoes the last update of Algorithm 1 and redoes it from the stored iterate
+ * and direction with step lengths alpha_p (X) and alpha_d (Y, T, Z); a
+ * negative value keeps that step length. The result is rounded like every
+ * update (Corollary psdness_rounding). Meant for exercising the safeguards of
+ * Section 3.5: an update planted past the boundary of the cone is found by
+ * the next step-length solve and repaired by damp-and-retry. Returns
+ * TT_E_INVALID_ARG before the first update. */
+tt_status tt_sdp_redo_update(tt_sdp_ctx* ctx, double alpha_p, double alpha_d);
+
+/* Iterates until the stopping rules hold or max_iters. For a batch context
+ * (tt_sdp_create_batch) `out` is an array of tt_sdp_batch_size(ctx) results
+ * and the status is that of tt_sdp_solve_batch. */
 tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out);
 
 /* Solves n independent contexts concurrently: `workers` host threads, each
@@ -317,7 +383,10 @@ tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out);
 tt_status tt_sdp_solve_batch(int32_t n, tt_sdp_ctx* const* ctxs, int32_t workers, tt_sdp_result* out);
 
 /* Copies iterate `which` (0 X, 1 Y, 2 T, 3 Z; TT matrices with 2 x 2 modes)
- * to the host. With cores == NULL only ranks (d+1 ints) and *count are set. */
+ * to the host. which = 4 gives the block-AMEn frame kept as the warm start of
+ * the next Newton solve (Section 3.5), a TT vector with mode 4 whose core 0
+ * carries block 0 (dX); its ranks are the frame's bond ranks. With
+ * cores == NULL only ranks (d+1 ints) and *count are set. */
 tt_status tt_sdp_get_iterate(tt_sdp_ctx* ctx, int32_t which, int32_t* ranks, double* cores,
                              size_t* count);
 

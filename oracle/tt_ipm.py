@@ -570,6 +570,7 @@ class IterInfo:
     direction: str = ""
     ranks_X: list = field(default_factory=list)
     ranks_Z: list = field(default_factory=list)
+    ranks_W: list = field(default_factory=list)   # frame kept as the next solve's warm start
     sweeps: int = 0
 
 
@@ -827,6 +828,7 @@ class TTIPM:
         self._apply_update()
         info.ranks_X = tt.ranks(self.X)
         info.ranks_Z = tt.ranks(self.Z)
+        info.ranks_W = tt.ranks(self.w.cores)
         return info
 
     def _mehrotra(self, direction: str, mu: float, zero_p: bool, zero_d: bool):

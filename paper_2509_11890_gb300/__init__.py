@@ -19,7 +19,8 @@ FP64, FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
 __all__ = [
     "FP64", "FP32", "MIXED_TF32", "MIXED_BF16", "TTSDPError", "lib",
     "env_left_step", "env_right_step", "local_apply", "local_matrix",
-    "hadamard", "matvec", "inner", "round_tt", "tt_from_dense", "default_options", "Context",
+    "hadamard", "matvec", "inner", "round_tt", "round_sdp", "tt_from_dense", "default_options", "Context", "Batch",
+    "make_allocator",
     "launch_count", "contraction_stats", "contraction_stats_reset",
 ]
 
@@ -229,12 +230,80 @@ class _HostTT:
                                 self.flat.ctypes.data_as(ctypes.c_void_p))
 
 
+def _problem(parts: dict):
+    """tt_sdp_problem from host cores: C (r, 2, 2, r'), A_eq and K_y (r, 4, 4, r'),
+    B_eq (r, 4, r'), optional A_ineq, B_ineq, K_t, ones_t, ineq_sign, q, lam0, lam0_ineq."""
+    keep = []
+
+    def desc(name, m, n):
+        cores = parts.get(name)
+        if cores is None:
+            return _lib.TTDesc(0, None, m, n, None)
+        h = _HostTT(cores, m, n)
+        keep.append(h)
+        return h.desc
+
+    pr = _lib.Problem(desc("C", 2, 2), desc("A_eq", 4, 4), desc("B_eq", 4, 1), desc("K_y", 4, 4),
+                      desc("A_ineq", 4, 4), desc("B_ineq", 4, 1), desc("K_t", 4, 4), desc("ones_t", 2, 2),
+                      int(parts.get("ineq_sign", 1)), int(parts.get("q", 0)), float(parts.get("lam0", 1.0)),
+                      float(parts.get("lam0_ineq", 1e-3)))
+    return pr, keep
+
+
+def make_allocator(alloc, free, user=None):
+    """A tt_allocator from two Python callables alloc(nbytes, stream) -> int pointer
+    and free(ptr, stream). Keep the returned object alive while contexts use it."""
+    a = _lib.Allocator(_lib.ALLOC_FN(lambda n, st, u: alloc(int(n), st) or None),
+                       _lib.FREE_FN(lambda ptr, st, u: free(ptr, st)), user)
+    return a
+
+
+def round_sdp(cores, tol, cap=0, psd_shift=0, stream=None):
+    """tt_sdp_round on host cores (r, m, n, r') or (r, m, r'): TT rounding plus
+    the spectral shift (0 none, 1 zeta I, 2 zeta (J - I)). Returns (cores, zeta)."""
+    c0 = np.asarray(cores[0])
+    mat = c0.ndim == 4
+    m = c0.shape[1]
+    n = c0.shape[2] if mat else 1
+    h = _HostTT(cores, m, n)
+    d = len(cores)
+    ranks = (ctypes.c_int32 * (d + 1))()
+    out = _lib.TTDesc(d, ctypes.cast(ranks, _lib.P_int32), m, n, None)
+    zeta = ctypes.c_double(0.0)
+    _check(lib().tt_sdp_round(ctypes.byref(h.desc), float(tol), int(cap), int(psd_shift), ctypes.byref(out),
+                              ctypes.byref(zeta), _stream(stream)), "tt_sdp_round")
+    r = list(ranks)
+    buf = np.empty(_count(r, m, n), dtype=np.float64)
+    out.cores = buf.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().tt_sdp_round(ctypes.byref(h.desc), float(tol), int(cap), int(psd_shift), ctypes.byref(out),
+                              ctypes.byref(zeta), _stream(stream)), "tt_sdp_round")
+    assert list(ranks) == r
+    res, off = [], 0
+    for k in range(d):
+        shape = (r[k], m, n, r[k + 1]) if mat else (r[k], m, r[k + 1])
+        size = int(np.prod(shape))
+        res.append(buf[off:off + size].reshape(shape).copy())
+        off += size
+    return res, zeta.value
+
+
 class Context:
     """One SDP in TT form with its iterates on the device (tt_sdp_ctx)."""
 
     def __init__(self, handle, keep):
         self._h = handle
         self._keep = keep
+
+    @staticmethod
+    def create(parts: dict, options=None, allocator=None, stream=None):
+        """tt_sdp_create from host cores (see _problem); allocator from make_allocator or None."""
+        pr, keep = _problem(parts)
+        o = options or default_options()
+        h = ctypes.c_void_p()
+        _check(lib().tt_sdp_create(ctypes.byref(pr), ctypes.byref(o),
+                                   ctypes.byref(allocator) if allocator is not None else None, _stream(stream),
+                                   ctypes.byref(h)), "tt_sdp_create")
+        return Context(h, keep + [allocator])
 
     @staticmethod
     def maxcut(weight_cores, options=None, stream=None):
@@ -268,6 +337,10 @@ class Context:
         _check(lib().tt_sdp_newton_step(self._h, ctypes.byref(info)), "tt_sdp_newton_step")
         return {f: getattr(info, f) for f, _ in _lib.IterInfo._fields_}
 
+    def redo_update(self, alpha_p: float = -1.0, alpha_d: float = -1.0):
+        """tt_sdp_redo_update: redo the last update with other step lengths (negative keeps one)."""
+        _check(lib().tt_sdp_redo_update(self._h, float(alpha_p), float(alpha_d)), "tt_sdp_redo_update")
+
     def solve(self) -> dict:
         res = _lib.Result()
         st = lib().tt_sdp_solve(self._h, ctypes.byref(res))
@@ -275,6 +348,14 @@ class Context:
         if st not in (0, 7):
             _check(st, "tt_sdp_solve")
         return out
+
+    def ranks(self, which: int):
+        """Bond ranks (d + 1 ints) of X (0), Y (1), T (2), Z (3) or the AMEn frame (4)."""
+        d = lib().tt_sdp_order(self._h)
+        ranks = (ctypes.c_int32 * (d + 1))()
+        cnt = ctypes.c_size_t(0)
+        _check(lib().tt_sdp_get_iterate(self._h, which, ranks, None, ctypes.byref(cnt)), "tt_sdp_get_iterate")
+        return list(ranks)
 
     def iterate(self, which: int):
         """Cores (host numpy, r x 2 x 2 x r') of X (0), Y (1), T (2) or Z (3)."""
@@ -308,6 +389,54 @@ class Context:
         if n.value:
             _check(lib().tt_sdp_get_trace(self._h, X.ctypes.data, t.ctypes.data, ctypes.byref(n)), "tt_sdp_get_trace")
         return X, t
+
+    def close(self):
+        if self._h and not getattr(self, "_borrowed", False):
+            lib().tt_sdp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """n independent SDPs in one batch context (tt_sdp_create_batch)."""
+
+    def __init__(self, parts_list, options=None, allocator=None, stream=None):
+        n = len(parts_list)
+        probs = (_lib.Problem * n)()
+        self._keep = [allocator]
+        for i, parts in enumerate(parts_list):
+            probs[i], k = _problem(parts)
+            self._keep += k
+        o = options or default_options()
+        self._h = ctypes.c_void_p()
+        _check(lib().tt_sdp_create_batch(n, probs, ctypes.byref(o),
+                                         ctypes.byref(allocator) if allocator is not None else None,
+                                         _stream(stream), ctypes.byref(self._h)), "tt_sdp_create_batch")
+
+    def __len__(self):
+        return int(lib().tt_sdp_batch_size(self._h))
+
+    def solve(self):
+        n = len(self)
+        res = (_lib.Result * n)()
+        st = lib().tt_sdp_solve(self._h, res)
+        if st not in (0, 7):
+            _check(st, "tt_sdp_solve")
+        return [{f: getattr(r, f) for f, _ in _lib.Result._fields_} for r in res]
+
+    def member(self, i: int) -> Context:
+        """Instance i as a borrowed Context (do not close it; the batch owns it)."""
+        h = lib().tt_sdp_batch_member(self._h, int(i))
+        if not h:
+            raise IndexError(i)
+        c = Context(ctypes.c_void_p(h), [self])
+        c._borrowed = True
+        return c
 
     def close(self):
         if self._h:

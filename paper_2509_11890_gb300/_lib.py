@@ -49,6 +49,14 @@ class IterInfo(ctypes.Structure):
                 ("xz_fallbacks", ctypes.c_int64)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p, c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("status", c_int32), ("iters", c_int32), ("pobj", c_double), ("dobj", c_double),
                 ("rel_gap", c_double), ("rel_p", c_double), ("rel_d", c_double), ("seconds", c_double)]
@@ -77,7 +85,14 @@ SIGNATURES = {
     "tt_from_dense": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_int32, P_int32, c_void_p,
                                 ctypes.POINTER(c_size_t), c_void_p]),
     "tt_sdp_default_options": (None, [ctypes.POINTER(Options)]),
-    "tt_sdp_create": (c_int32, [ctypes.POINTER(Problem), ctypes.POINTER(Options), c_void_p, ctypes.POINTER(c_void_p)]),
+    "tt_sdp_create": (c_int32, [ctypes.POINTER(Problem), ctypes.POINTER(Options), ctypes.POINTER(Allocator), c_void_p,
+                                ctypes.POINTER(c_void_p)]),
+    "tt_sdp_create_batch": (c_int32, [c_int32, ctypes.POINTER(Problem), ctypes.POINTER(Options),
+                                      ctypes.POINTER(Allocator), c_void_p, ctypes.POINTER(c_void_p)]),
+    "tt_sdp_batch_size": (c_int32, [c_void_p]),
+    "tt_sdp_batch_member": (c_void_p, [c_void_p, c_int32]),
+    "tt_sdp_round": (c_int32, [ctypes.POINTER(TTDesc), c_double, c_int32, c_int32, ctypes.POINTER(TTDesc), P_double,
+                               c_void_p]),
     "tt_sdp_create_maxcut": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(Options), c_void_p,
                                        ctypes.POINTER(c_void_p)]),
     "tt_sdp_create_theta": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(Options), c_void_p,
@@ -86,6 +101,7 @@ SIGNATURES = {
                                    ctypes.POINTER(Options), c_void_p, ctypes.POINTER(c_void_p)]),
     "tt_sdp_newton_step": (c_int32, [c_void_p, ctypes.POINTER(IterInfo)]),
     "tt_sdp_solve": (c_int32, [c_void_p, ctypes.POINTER(Result)]),
+    "tt_sdp_redo_update": (c_int32, [c_void_p, c_double, c_double]),
     "tt_sdp_solve_batch": (c_int32, [c_int32, ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(Result)]),
     "tt_sdp_get_iterate": (c_int32, [c_void_p, c_int32, P_int32, c_void_p, ctypes.POINTER(c_size_t)]),
     "tt_sdp_order": (c_int32, [c_void_p]),

@@ -124,7 +124,32 @@ Options to_options(const tt_sdp_options* o) {
 struct tt_sdp_ctx {
   cudaStream_t stream;
   std::unique_ptr<Solver> solver;
+  tt_allocator alloc{nullptr, nullptr, nullptr};
+  bool has_alloc = false;
+  std::vector<tt_sdp_ctx*> members;  // a batch context owns its instances
+  bool batch = false;
+  const tt_allocator* allocator() const { return has_alloc ? &alloc : nullptr; }
 };
+
+namespace {
+// Scope of a call on a context: its stream and its allocator
+struct AllocGuard {
+  const tt_allocator* prev;
+  explicit AllocGuard(const tt_allocator* a) : prev(AllocScope::current()) { AllocScope::current() = a; }
+  ~AllocGuard() { AllocScope::current() = prev; }
+};
+
+template <typename F>
+tt_status ctx_guarded(tt_sdp_ctx* ctx, F&& fn) {
+  AllocGuard ag(ctx->allocator());
+  return guarded(ctx->stream, std::forward<F>(fn));
+}
+
+tt_allocator copy_allocator(const tt_allocator* a) {
+  TT_CHECK(!a || (a->alloc && a->free), TT_E_INVALID_ARG, "tt_allocator needs both alloc and free");
+  return a ? *a : tt_allocator{nullptr, nullptr, nullptr};
+}
+}  // namespace
 
 extern "C" {
 
@@ -273,6 +298,33 @@ tt_status tt_round(const tt_desc* in, double delta, int32_t rank_cap, int32_t* r
   });
 }
 
+tt_status tt_sdp_round(const tt_desc* in, double tol, int32_t rank_cap, int32_t psd_shift, tt_desc* out,
+                       double* zeta_out, void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(out && out->ranks && zeta_out && tol >= 0.0 && psd_shift >= 0 && psd_shift <= 2, TT_E_INVALID_ARG,
+             "bad tt_sdp_round arguments");
+    const DTT a = desc_host(in);
+    TT_CHECK(psd_shift == 0 || a.m == a.n, TT_E_SHAPE, "a spectral shift needs a square TT matrix");
+    // shift S of Corollary psdness_rounding: I for X and Z, J - I for T
+    DTT S;
+    double sn = 0.0;
+    if (psd_shift == 1) S = tt_identity(a.d, a.m);
+    if (psd_shift == 2) S = tt_add(tt_ones_mat(a.d, a.m), tt_identity(a.d, a.m), 1.0, -1.0);
+    if (psd_shift) sn = tt_norm(S);
+    auto rz = tt_round(a.view(a.m * a.n, 1), tol / (1.0 + sn), rank_cap);
+    DTT r = rz.first.view(a.m, a.n);
+    if (psd_shift && rz.second > 0.0) r = tt_add(r, S, 1.0, rz.second);
+    int32_t* ranks = const_cast<int32_t*>(out->ranks);
+    for (int k = 0; k <= r.d; ++k) ranks[k] = r.r[k];
+    out->d = r.d;
+    out->m = r.m;
+    out->n = r.n;
+    if (out->cores) tt_to_host(r, const_cast<double*>(out->cores));
+    *zeta_out = rz.second;
+    TT_CUDA(sync_stream(cur_stream()));
+  });
+}
+
 tt_status tt_from_dense(const double* dense, int32_t d, int32_t n, double eps_rel, int32_t rank_cap,
                         int32_t* ranks_out, double* cores_out, size_t* count, void* stream) {
   return guarded(stream, [&] {
@@ -313,25 +365,42 @@ void tt_sdp_default_options(tt_sdp_options* o) {
   o->time_limit = 0.0;
 }
 
-static tt_status make_ctx(Problem p, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
-  return guarded(stream, [&] {
+}  // extern "C"
+
+// Creates a context whose problem `build` assembles on the device. The
+// allocator struct is copied into the context first, so that every buffer
+// (the problem's included) refers to the context's own copy.
+template <typename B>
+static tt_status make_ctx(B&& build, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out,
+                          const tt_allocator* allocator = nullptr) {
+  auto* ctx = new tt_sdp_ctx;
+  ctx->stream = (cudaStream_t)stream;
+  tt_status s = guarded(stream, [&] {
     TT_CHECK(out, TT_E_INVALID_ARG, "null output");
+    ctx->alloc = copy_allocator(allocator);
+    ctx->has_alloc = allocator != nullptr;
     Options o = to_options(opts);
-    auto* ctx = new tt_sdp_ctx;
-    ctx->stream = (cudaStream_t)stream;
-    try {
-      ctx->solver = std::make_unique<Solver>(std::move(p), o);
-    } catch (...) {
-      delete ctx;
-      throw;
-    }
+    AllocGuard ag(ctx->allocator());
+    Problem p = build();
+    ctx->solver = std::make_unique<Solver>(std::move(p), o);
     *out = ctx;
   });
+  if (s != TT_OK) {
+    try {
+      AllocGuard ag(ctx->allocator());
+      StreamGuard g(stream);
+      ctx->solver.reset();
+    } catch (...) {
+    }
+    delete ctx;
+  }
+  return s;
 }
 
-tt_status tt_sdp_create(const tt_sdp_problem* prob, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
+// The Problem of a tt_sdp_problem (host cores copied to the device)
+static Problem problem_from(const tt_sdp_problem* prob) {
   Problem p;
-  tt_status s = guarded(stream, [&] {
+  {
     TT_CHECK(prob, TT_E_INVALID_ARG, "null problem");
     p.d = prob->C.d;
     p.C = desc_host(&prob->C);
@@ -352,47 +421,80 @@ tt_status tt_sdp_create(const tt_sdp_problem* prob, const tt_sdp_options* opts, 
     }
     p.lam0 = prob->lam0 > 0 ? prob->lam0 : 1.0;
     p.lam0_ineq = prob->lam0_ineq > 0 ? prob->lam0_ineq : 1e-3;
-  });
-  if (s != TT_OK) return s;
-  return make_ctx(std::move(p), opts, stream, out);
+  }
+  return p;
+}
+
+extern "C" {
+
+tt_status tt_sdp_create(const tt_sdp_problem* prob, const tt_sdp_options* opts, const tt_allocator* allocator,
+                        void* stream, tt_sdp_ctx** out) {
+  return make_ctx([&] { return problem_from(prob); }, opts, stream, out, allocator);
+}
+
+tt_status tt_sdp_create_batch(int32_t n, const tt_sdp_problem* probs, const tt_sdp_options* opts,
+                              const tt_allocator* allocator, void* stream, tt_sdp_ctx** out) {
+  if (n <= 0 || !probs || !out) return TT_E_INVALID_ARG;
+  auto* b = new tt_sdp_ctx;
+  b->stream = (cudaStream_t)stream;
+  b->batch = true;
+  for (int i = 0; i < n; ++i) {
+    tt_sdp_ctx* c = nullptr;
+    tt_status s = tt_sdp_create(&probs[i], opts, allocator, stream, &c);
+    if (s != TT_OK) {
+      for (tt_sdp_ctx* m : b->members) tt_sdp_destroy(m);
+      delete b;
+      return s;
+    }
+    b->members.push_back(c);
+  }
+  *out = b;
+  return TT_OK;
+}
+
+int32_t tt_sdp_batch_size(const tt_sdp_ctx* ctx) {
+  if (!ctx) return 0;
+  return ctx->batch ? (int32_t)ctx->members.size() : 1;
+}
+
+tt_sdp_ctx* tt_sdp_batch_member(tt_sdp_ctx* ctx, int32_t i) {
+  if (!ctx || !ctx->batch || i < 0 || i >= (int32_t)ctx->members.size()) return nullptr;
+  return ctx->members[(size_t)i];
 }
 
 tt_status tt_sdp_create_maxcut(const tt_desc* weights, const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
-  Problem p;
-  tt_status s = guarded(stream, [&] {
-    TT_CHECK(weights && weights->m == 2 && weights->n == 2, TT_E_SHAPE, "weights must have 2 x 2 modes");
-    p = build_maxcut(desc_host(weights));
-  });
-  if (s != TT_OK) return s;
-  return make_ctx(std::move(p), opts, stream, out);
+  return make_ctx(
+      [&] {
+        TT_CHECK(weights && weights->m == 2 && weights->n == 2, TT_E_SHAPE, "weights must have 2 x 2 modes");
+        return build_maxcut(desc_host(weights));
+      },
+      opts, stream, out);
 }
 
 tt_status tt_sdp_create_theta(const tt_desc* adjacency, const tt_sdp_options* opts, void* stream,
                               tt_sdp_ctx** out) {
-  Problem p;
-  tt_status s = guarded(stream, [&] {
-    TT_CHECK(adjacency && adjacency->m == 2 && adjacency->n == 2, TT_E_SHAPE, "adjacency must have 2 x 2 modes");
-    p = build_theta(desc_host(adjacency));
-  });
-  if (s != TT_OK) return s;
-  return make_ctx(std::move(p), opts, stream, out);
+  return make_ctx(
+      [&] {
+        TT_CHECK(adjacency && adjacency->m == 2 && adjacency->n == 2, TT_E_SHAPE, "adjacency must have 2 x 2 modes");
+        return build_theta(desc_host(adjacency));
+      },
+      opts, stream, out);
 }
 
 tt_status tt_sdp_create_cc(const tt_desc* c_plus, const tt_desc* c_minus, const tt_desc* adjacency,
                            const tt_sdp_options* opts, void* stream, tt_sdp_ctx** out) {
-  Problem p;
-  tt_status s = guarded(stream, [&] {
-    for (const tt_desc* t : {c_plus, c_minus, adjacency})
-      TT_CHECK(t && t->m == 2 && t->n == 2, TT_E_SHAPE, "inputs must have 2 x 2 modes");
-    p = build_cc(desc_host(c_plus), desc_host(c_minus), desc_host(adjacency));
-  });
-  if (s != TT_OK) return s;
-  return make_ctx(std::move(p), opts, stream, out);
+  return make_ctx(
+      [&] {
+        for (const tt_desc* t : {c_plus, c_minus, adjacency})
+          TT_CHECK(t && t->m == 2 && t->n == 2, TT_E_SHAPE, "inputs must have 2 x 2 modes");
+        return build_cc(desc_host(c_plus), desc_host(c_minus), desc_host(adjacency));
+      },
+      opts, stream, out);
 }
 
 tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info) {
-  if (!ctx || !info) return TT_E_INVALID_ARG;
-  return guarded(ctx->stream, [&] {
+  if (!ctx || !info || ctx->batch) return TT_E_INVALID_ARG;
+  return ctx_guarded(ctx, [&] {
     IterLog l = ctx->solver->iterate();
     info->iter = l.iter;
     info->converged = l.converged;
@@ -417,6 +519,13 @@ tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info) {
     info->forcing_corrections = l.forcing_corrections;
     info->damped_retries = l.retries;
     info->xz_fallbacks = l.fallbacks;
+  });
+}
+
+tt_status tt_sdp_redo_update(tt_sdp_ctx* ctx, double alpha_p, double alpha_d) {
+  if (!ctx || ctx->batch) return TT_E_INVALID_ARG;
+  return ctx_guarded(ctx, [&] {
+    TT_CHECK(ctx->solver->redo_update(alpha_p, alpha_d), TT_E_INVALID_ARG, "no update to redo yet");
   });
 }
 
@@ -449,6 +558,11 @@ static tt_status solve_loop(tt_sdp_ctx* ctx, tt_sdp_result* out) {
 
 tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out) {
   if (!ctx || !out) return TT_E_INVALID_ARG;
+  if (ctx->batch) {
+    const int32_t n = (int32_t)ctx->members.size();
+    std::memset(out, 0, sizeof(*out) * (size_t)n);
+    return tt_sdp_solve_batch(n, ctx->members.data(), n < 16 ? n : 16, out);
+  }
   std::memset(out, 0, sizeof(*out));
   ctx->solver->set_deadline(ctx->solver->options().time_limit);
   const tt_status s = solve_loop(ctx, out);
@@ -457,12 +571,15 @@ tt_status tt_sdp_solve(tt_sdp_ctx* ctx, tt_sdp_result* out) {
 }
 
 tt_status tt_sdp_get_iterate(tt_sdp_ctx* ctx, int32_t which, int32_t* ranks, double* cores, size_t* count) {
-  if (!ctx || !ranks || !count) return TT_E_INVALID_ARG;
-  return guarded(ctx->stream, [&] {
-    TT_CHECK(which >= 0 && which <= 3, TT_E_INVALID_ARG, "which must be 0..3");
+  if (!ctx || !ranks || !count || ctx->batch) return TT_E_INVALID_ARG;
+  return ctx_guarded(ctx, [&] {
+    TT_CHECK(which >= 0 && which <= 4, TT_E_INVALID_ARG, "which must be 0..4");
     TT_CHECK(which != 2 || ctx->solver->has_ineq(), TT_E_INVALID_ARG, "no inequality multiplier");
+    TT_CHECK(which != 4 || ctx->solver->frame(), TT_E_INVALID_ARG, "no Newton solve has run yet");
+    DTT fr;
+    if (which == 4) fr = ctx->solver->frame()->component(0);
     const DTT& t = which == 0 ? ctx->solver->X() : which == 1 ? ctx->solver->Y()
-                                                  : which == 2 ? ctx->solver->T() : ctx->solver->Z();
+                 : which == 2 ? ctx->solver->T() : which == 3 ? ctx->solver->Z() : fr;
     for (int k = 0; k <= t.d; ++k) ranks[k] = t.r[k];
     size_t need = t.count();
     if (cores) {
@@ -473,12 +590,18 @@ tt_status tt_sdp_get_iterate(tt_sdp_ctx* ctx, int32_t which, int32_t* ranks, dou
   });
 }
 
-int32_t tt_sdp_order(const tt_sdp_ctx* ctx) { return ctx ? ctx->solver->order() : 0; }
+int32_t tt_sdp_order(const tt_sdp_ctx* ctx) {
+  if (!ctx) return 0;
+  if (ctx->batch) return ctx->members.empty() ? 0 : ctx->members[0]->solver->order();
+  return ctx->solver->order();
+}
 
 void tt_sdp_destroy(tt_sdp_ctx* ctx) {
   if (!ctx) return;
+  for (tt_sdp_ctx* m : ctx->members) tt_sdp_destroy(m);
   try {
     StreamGuard g(ctx->stream);
+    AllocGuard ag(ctx->allocator());
     ctx->solver.reset();
     sync_stream(ctx->stream);
   } catch (...) {

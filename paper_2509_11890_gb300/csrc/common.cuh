@@ -51,7 +51,18 @@ struct StreamScope {
 };
 inline cudaStream_t cur_stream() { return StreamScope::current(); }
 
-// Device buffer allocated stream-ordered from the device's default memory pool.
+// The caller's device allocator (tt_allocator) while a call on its context
+// runs on this thread; null: the device's default stream-ordered pool.
+struct AllocScope {
+  static const tt_allocator*& current() {
+    static thread_local const tt_allocator* a = nullptr;
+    return a;
+  }
+};
+
+// Device buffer allocated stream-ordered from the device's default memory
+// pool, or from the caller's allocator when one is in scope (the buffer
+// remembers which, and frees through the same one).
 template <typename T>
 class DBuf {
  public:
@@ -59,19 +70,32 @@ class DBuf {
   explicit DBuf(size_t n) { alloc(n); }
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
-  DBuf(DBuf&& o) noexcept : p_(o.p_), n_(o.n_) { o.p_ = nullptr; o.n_ = 0; }
+  DBuf(DBuf&& o) noexcept : p_(o.p_), n_(o.n_), al_(o.al_) { o.p_ = nullptr; o.n_ = 0; }
   DBuf& operator=(DBuf&& o) noexcept {
-    if (this != &o) { release(); p_ = o.p_; n_ = o.n_; o.p_ = nullptr; o.n_ = 0; }
+    if (this != &o) { release(); p_ = o.p_; n_ = o.n_; al_ = o.al_; o.p_ = nullptr; o.n_ = 0; }
     return *this;
   }
   ~DBuf() { release(); }
   void alloc(size_t n) {
     release();
     n_ = n;
-    if (n) TT_CUDA(cudaMallocAsync((void**)&p_, n * sizeof(T), cur_stream()));
+    al_ = AllocScope::current();
+    if (!n) return;
+    if (al_) {
+      p_ = static_cast<T*>(al_->alloc(n * sizeof(T), (void*)cur_stream(), al_->user));
+      if (!p_) {
+        n_ = 0;
+        throw TTError(TT_E_NOMEM, "the caller's allocator returned NULL");
+      }
+    } else {
+      TT_CUDA(cudaMallocAsync((void**)&p_, n * sizeof(T), cur_stream()));
+    }
   }
   void release() {
-    if (p_) cudaFreeAsync(p_, cur_stream());
+    if (p_) {
+      if (al_) al_->free(p_, (void*)cur_stream(), al_->user);
+      else cudaFreeAsync(p_, cur_stream());
+    }
     p_ = nullptr;
     n_ = 0;
   }
@@ -81,6 +105,7 @@ class DBuf {
  private:
   T* p_ = nullptr;
   size_t n_ = 0;
+  const tt_allocator* al_ = nullptr;
 };
 
 // Counts kernel launches issued by the library (reported by the benchmark).

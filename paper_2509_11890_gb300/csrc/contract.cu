@@ -32,6 +32,82 @@ int grid_for(long long n) {
   return (int)(g < 152 * 16 ? (g < 1 ? 1 : g) : 152 * 16);
 }
 
+// Per-core norm scaling of the reduced-precision contractions: every FP64
+// operand is scaled to unit Frobenius norm before it is rounded to FP32 (and
+// from there to TF32 or BF16 on the tensor cores), and the FP64 result is
+// multiplied back by the product of the norms, kept in FP64. The contraction
+// is linear in each operand, so the scaling changes only the rounding: every
+// operand's entries are O(1) whatever the magnitude of the iterate.
+constexpr int kMaxOps = 4;
+struct OpSet {
+  const double* src[kMaxOps];
+  float* dst[kMaxOps];
+  long long n[kMaxOps];
+  int count;
+};
+
+// nrm2[k] += sum of squares of operand blockIdx.y (nrm2 zeroed beforehand)
+__global__ void sumsq_kernel(OpSet ops, double* nrm2) {
+  const int k = blockIdx.y;
+  const double* a = ops.src[k];
+  const long long n = ops.n[k];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += a[i] * a[i];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0 && s != 0.0) atomicAdd(&nrm2[k], s);
+  }
+}
+
+// dst = (float)(src / ||src||) for operand blockIdx.y (unscaled when the norm is 0)
+__global__ void to_float_scaled_kernel(OpSet ops, const double* __restrict__ nrm2) {
+  const int k = blockIdx.y;
+  const double v = nrm2[k];
+  const double inv = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+  const double* a = ops.src[k];
+  float* b = ops.dst[k];
+  const long long n = ops.n[k];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)(a[i] * inv);
+}
+
+// out = (double)e * prod_k ||operand k|| (the norms of the operands that were scaled)
+__global__ void to_double_scaled_kernel(const float* __restrict__ e, double* __restrict__ out, long long n,
+                                        const double* __restrict__ nrm2, int count) {
+  double s = 1.0;
+  for (int k = 0; k < count; ++k) s *= nrm2[k] > 0.0 ? sqrt(nrm2[k]) : 1.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)e[i] * s;
+}
+
+// Scaled conversion of up to four operands; returns the device array of
+// their squared norms (owned by the caller's scratch `nrm2`).
+void to_float_scaled(const OpSet& ops, double* nrm2, cudaStream_t st) {
+  long long mx = 1;
+  for (int k = 0; k < ops.count; ++k) mx = ops.n[k] > mx ? ops.n[k] : mx;
+  TT_CUDA(cudaMemsetAsync(nrm2, 0, sizeof(double) * kMaxOps, st));
+  const int gx = grid_for(mx) < 64 ? grid_for(mx) : 64;
+  sumsq_kernel<<<dim3(gx, ops.count), 256, 0, st>>>(ops, nrm2);
+  count_launch();
+  check_launch("sumsq_kernel");
+  to_float_scaled_kernel<<<dim3(grid_for(mx), ops.count), 256, 0, st>>>(ops, nrm2);
+  count_launch();
+  check_launch("to_float_scaled_kernel");
+}
+
+void to_double_scaled(const float* e, double* out, long long n, const double* nrm2, int count, cudaStream_t st) {
+  if (n <= 0) return;
+  to_double_scaled_kernel<<<grid_for(n), 256, 0, st>>>(e, out, n, nrm2, count);
+  count_launch();
+  check_launch("to_double_scaled_kernel");
+}
+
 }  // namespace
 
 void to_float(const double* a, float* b, long long n, cudaStream_t st) {
@@ -226,6 +302,7 @@ namespace {
 
 struct F32Scratch {
   DBuf<float> a, b, c, d, e, t1, t2;
+  DBuf<double> nrm;  // squared Frobenius norms of the scaled operands
 };
 
 size_t sz_phi(const CDims& d) { return (size_t)d.rw * d.R * d.rv; }
@@ -252,12 +329,13 @@ void env_left_step(const CDims& d, const double* phi, const double* u, const dou
   } else {
     F32Scratch s;
     s.a.alloc(sz_phi(d)); s.b.alloc(sz_u(d)); s.c.alloc(sz_op(d)); s.d.alloc(sz_v(d));
-    s.e.alloc(sz_psi(d)); s.t1.alloc(t1n); s.t2.alloc(t2n);
-    to_float(phi, s.a.get(), sz_phi(d), st); to_float(u, s.b.get(), sz_u(d), st);
-    to_float(op, s.c.get(), sz_op(d), st); to_float(v, s.d.get(), sz_v(d), st);
+    s.e.alloc(sz_psi(d)); s.t1.alloc(t1n); s.t2.alloc(t2n); s.nrm.alloc(kMaxOps);
+    to_float_scaled(OpSet{{phi, u, op, v}, {s.a.get(), s.b.get(), s.c.get(), s.d.get()},
+                          {(long long)sz_phi(d), (long long)sz_u(d), (long long)sz_op(d), (long long)sz_v(d)}, 4},
+                    s.nrm.get(), st);
     env_left_t<float>(d, s.a.get(), s.b.get(), s.c.get(), s.d.get(), s.e.get(), s.t1.get(),
                       s.t2.get(), st, prec);
-    to_double(s.e.get(), out, sz_psi(d), st);
+    to_double_scaled(s.e.get(), out, (long long)sz_psi(d), s.nrm.get(), 4, st);
   }
   stats_end(st, contract_flops(d));
 }
@@ -273,12 +351,13 @@ void env_right_step(const CDims& d, const double* psi, const double* u, const do
   } else {
     F32Scratch s;
     s.a.alloc(sz_psi(d)); s.b.alloc(sz_u(d)); s.c.alloc(sz_op(d)); s.d.alloc(sz_v(d));
-    s.e.alloc(sz_phi(d)); s.t1.alloc(t1n); s.t2.alloc(t2n);
-    to_float(psi, s.a.get(), sz_psi(d), st); to_float(u, s.b.get(), sz_u(d), st);
-    to_float(op, s.c.get(), sz_op(d), st); to_float(v, s.d.get(), sz_v(d), st);
+    s.e.alloc(sz_phi(d)); s.t1.alloc(t1n); s.t2.alloc(t2n); s.nrm.alloc(kMaxOps);
+    to_float_scaled(OpSet{{psi, u, op, v}, {s.a.get(), s.b.get(), s.c.get(), s.d.get()},
+                          {(long long)sz_psi(d), (long long)sz_u(d), (long long)sz_op(d), (long long)sz_v(d)}, 4},
+                    s.nrm.get(), st);
     env_right_t<float>(d, s.a.get(), s.b.get(), s.c.get(), s.d.get(), s.e.get(), s.t1.get(),
                        s.t2.get(), st);
-    to_double(s.e.get(), out, sz_phi(d), st);
+    to_double_scaled(s.e.get(), out, (long long)sz_phi(d), s.nrm.get(), 4, st);
   }
   stats_end(st, contract_flops(d));
 }
@@ -295,12 +374,13 @@ void local_apply(const CDims& d, const double* phi, const double* op, const doub
   } else {
     F32Scratch s;
     s.a.alloc(sz_phi(d)); s.b.alloc(sz_psi(d)); s.c.alloc(sz_op(d)); s.d.alloc(sz_v(d));
-    s.e.alloc(yn); s.t1.alloc(t1n); s.t2.alloc(t2n);
-    to_float(phi, s.a.get(), sz_phi(d), st); to_float(psi, s.b.get(), sz_psi(d), st);
-    to_float(op, s.c.get(), sz_op(d), st); to_float(x, s.d.get(), sz_v(d), st);
+    s.e.alloc(yn); s.t1.alloc(t1n); s.t2.alloc(t2n); s.nrm.alloc(kMaxOps);
+    to_float_scaled(OpSet{{phi, psi, op, x}, {s.a.get(), s.b.get(), s.c.get(), s.d.get()},
+                          {(long long)sz_phi(d), (long long)sz_psi(d), (long long)sz_op(d), (long long)sz_v(d)}, 4},
+                    s.nrm.get(), st);
     apply_t<float>(d, s.a.get(), s.c.get(), s.b.get(), s.d.get(), s.e.get(), s.t1.get(),
                    s.t2.get(), st, prec);
-    to_double(s.e.get(), y, yn, st);
+    to_double_scaled(s.e.get(), y, (long long)yn, s.nrm.get(), 4, st);
   }
   stats_end(st, contract_flops(d));
 }
@@ -316,11 +396,12 @@ void local_matrix(const CDims& d, const double* phi, const double* op, const dou
   } else {
     F32Scratch s;
     s.a.alloc(sz_phi(d)); s.b.alloc(sz_psi(d)); s.c.alloc(sz_op(d));
-    s.e.alloc(on); s.t1.alloc(t1n);
-    to_float(phi, s.a.get(), sz_phi(d), st); to_float(psi, s.b.get(), sz_psi(d), st);
-    to_float(op, s.c.get(), sz_op(d), st);
+    s.e.alloc(on); s.t1.alloc(t1n); s.nrm.alloc(kMaxOps);
+    to_float_scaled(OpSet{{phi, psi, op, nullptr}, {s.a.get(), s.b.get(), s.c.get(), nullptr},
+                          {(long long)sz_phi(d), (long long)sz_psi(d), (long long)sz_op(d), 0}, 3},
+                    s.nrm.get(), st);
     local_matrix_t<float>(d, s.a.get(), s.c.get(), s.b.get(), s.e.get(), s.t1.get(), st);
-    to_double(s.e.get(), out, on, st);
+    to_double_scaled(s.e.get(), out, (long long)on, s.nrm.get(), 3, st);
   }
 }
 

@@ -52,12 +52,14 @@ void run_concurrently(std::vector<std::function<void()>>& jobs, std::vector<cuda
   std::vector<std::exception_ptr> err(nj);
   for (size_t i = 1; i < nj; ++i) TT_CUDA(cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming));
   std::vector<std::thread> th;
+  const tt_allocator* al = AllocScope::current();
   for (size_t i = 1; i < nj; ++i) {
     cudaStream_t s = side[i - 1];
-    th.emplace_back([&, i, s]() {
+    th.emplace_back([&, i, s, al]() {
       try {
         TT_CUDA(cudaSetDevice(dev));
         StreamScope::current() = s;
+        AllocScope::current() = al;
         TT_CUDA(cudaStreamWaitEvent(s, start, 0));
         jobs[i]();
         TT_CUDA(cudaEventRecord(done[i], s));
@@ -720,6 +722,10 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
   }
   info->sweeps = sweep;
   info->max_change = max_change;
+  // FP64: the solve met its tolerance when the last sweep's largest block
+  // change is below it (a single sweep included, whose changes are measured
+  // against the warm start projected onto the new frames)
+  if (prec_in == TT_FP64) info->converged = max_change < tol;
   // the solution, exact, with the block index where the last sweep left it
   const bool at_end = (sweep % 2 == 1);
   BlockTT sol;
@@ -1408,6 +1414,14 @@ void Solver::apply_update() {
   Z_ = std::move(Zr);
   Y_ = std::move(Yr);
   if (p_.ineq) T_ = std::move(Tr);
+}
+
+bool Solver::redo_update(double alpha_p, double alpha_d) {
+  if (!last_.valid) return false;
+  if (alpha_p >= 0.0) last_.ap = alpha_p;
+  if (alpha_d >= 0.0) last_.ad = alpha_d;
+  apply_update();
+  return true;
 }
 
 IterLog Solver::iterate() {

@@ -70,6 +70,9 @@ class Solver {
   Solver(const Solver&) = delete;
   Solver& operator=(const Solver&) = delete;
   IterLog iterate();        // one iteration of Algorithm 1
+  // redo the last update from its stored iterate and direction with other
+  // step lengths (negative: keep that one); false when no update exists yet
+  bool redo_update(double alpha_p, double alpha_d);
   // wall-clock deadline checked between the core steps of the AMEn sweeps;
   // past it the iteration in progress throws TT_E_NO_CONVERGENCE
   void set_deadline(double seconds_from_now);
@@ -77,6 +80,8 @@ class Solver {
   const DTT& Y() const { return Y_; }
   const DTT& T() const { return T_; }
   const DTT& Z() const { return Z_; }
+  // frame of the last Newton solve's warm start (block index at core 0); null before the first
+  const BlockTT* frame() const { return w_.get(); }
   bool has_ineq() const { return p_.ineq; }
   int order() const { return p_.d; }
   int iter() const { return it_; }

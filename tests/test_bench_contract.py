@@ -59,3 +59,29 @@ def test_single_process_helpers():
     assert bench.gather_results({3: (0, 1.0, 4)}, 1) == {3: (0, 1.0, 4)}
     assert set(bench.WORKLOADS) >= {"maxcut_d10_kron_er_cap64", "maxcut_d6_kron_cap16",
                                      "maxcut_batch64_d6to11_cap64"}
+
+
+def test_dual_residual_bound_proves_the_weighted_workload_uncertifiable_at_cap_64():
+    # Kronecker OR Erdos-Renyi graph with weights U[0.5, 1.5], n = 2^10, cap 64:
+    # every iterate Z of TT rank <= 65 leaves rel_d above 0.2, three orders of
+    # magnitude above eps_d = 2e-4
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2509_11890_gb300 import inputs
+    w = inputs.maxcut_kron_er(10, 0)["weights"]
+    lb = bench.dual_residual_lower_bound(w, 64)
+    assert lb["rel_d_lower_bound"] > 0.2 and not lb["certifiable"]
+    assert lb["bond"] == 5
+    # the bound shrinks as the cap grows and vanishes once the cap covers
+    # every unfolding rank (at most 4^5 = 1024 at the middle bond)
+    assert bench.dual_residual_lower_bound(w, 256)["rel_d_lower_bound"] < lb["rel_d_lower_bound"]
+    assert bench.dual_residual_lower_bound(w, 1024)["rel_d_lower_bound"] == 0.0
+
+
+def test_dual_residual_bound_is_zero_for_low_rank_objectives():
+    # unit-weight Kronecker graphs: C has TT rank <= 4, nothing forces a residual
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2509_11890_gb300 import inputs
+    lb = bench.dual_residual_lower_bound(inputs.maxcut_kron(8, 0)["weights"], 16)
+    assert lb["rel_d_lower_bound"] < 1e-12 and lb["certifiable"]

@@ -1,9 +1,11 @@
 """Tensor-core (tcgen05, TF32 / BF16 inputs, FP32 accumulation) contractions against the oracle.
 
-Only the middle contraction stage runs on the tensor cores; tolerances follow
-from the input rounding: TF32 keeps 10 mantissa bits (unit roundoff 2^-11),
-BF16 7 (2^-8), so the relative error of a K-term sum of products with
-random signs stays within a few unit roundoffs: 5e-3 (TF32), 3e-2 (BF16).
+Tolerances follow from the input rounding: TF32 keeps 10 mantissa bits (unit
+roundoff 2^-11), BF16 7 (2^-8); every term of the contraction is a product of
+four rounded operands whose intermediate sums are rounded again between the
+stages (at most six roundings of 2^-11 or 2^-8 on each term), so every output
+entry stays within 5e-3 (TF32) or 3e-2 (BF16) of the exact value relative to
+the same contraction of the operands' absolute values, element by element.
 """
 import numpy as np
 import pytest
@@ -37,8 +39,12 @@ def _dims(s):
     return dict(zip(["rw", "rw2", "R", "R2", "rv", "rv2", "m", "n"], s))
 
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+def assert_bounded(got, ref, ref_abs, tol):
+    """|got - ref| <= tol * ref_abs, element by element."""
+    got = got.reshape(ref.shape)
+    bound = tol * ref_abs + 1e-300
+    bad = np.abs(got - ref) > bound
+    assert not bad.any(), (int(bad.sum()), float(np.max(np.abs(got - ref) / bound)))
 
 
 @pytest.mark.parametrize("prec", [tg.MIXED_TF32, tg.MIXED_BF16])
@@ -48,9 +54,39 @@ def test_env_left_step_tensor_cores(shape, prec):
     phi, u = _rand((rw, R, rv), 1), _rand((rw, m, rw2), 2)
     op, v = _rand((R, m, n, R2), 3), _rand((rv, n, rv2), 4)
     ref = tt.env_left_step(phi, u, op, v)
+    ref_abs = tt.env_left_step(np.abs(phi), np.abs(u), np.abs(op), np.abs(v))
     out = torch.empty(rw2 * R2 * rv2, dtype=torch.float64, device="cuda")
     tg.env_left_step(_dims(shape), _t(phi), _t(u), _t(op), _t(v), out, prec)
-    assert _rel(out.cpu().numpy().reshape(ref.shape), ref) <= TOL[prec]
+    assert_bounded(out.cpu().numpy(), ref, ref_abs, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [tg.MIXED_TF32, tg.MIXED_BF16])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_env_right_step_tensor_cores(shape, prec):
+    rw, rw2, R, R2, rv, rv2, m, n = shape
+    psi, u = _rand((rw2, R2, rv2), 5), _rand((rw, m, rw2), 6)
+    op, v = _rand((R, m, n, R2), 7), _rand((rv, n, rv2), 8)
+    ref = tt.env_right_step(psi, u, op, v)
+    ref_abs = tt.env_right_step(np.abs(psi), np.abs(u), np.abs(op), np.abs(v))
+    out = torch.empty(rw * R * rv, dtype=torch.float64, device="cuda")
+    tg.env_right_step(_dims(shape), _t(psi), _t(u), _t(op), _t(v), out, prec)
+    assert_bounded(out.cpu().numpy(), ref, ref_abs, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [tg.MIXED_TF32, tg.MIXED_BF16])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_scaled_operands_keep_the_relative_error(shape, prec):
+    # per-core norm scaling: operands far outside the FP32 range (1e-42 is
+    # below its smallest normal number, 1e+35 times 1e+25 above its largest)
+    # give the same relative error as unit-scaled ones
+    rw, rw2, R, R2, rv, rv2, m, n = shape
+    phi, u = _rand((rw, R, rv), 1) * 1e-42, _rand((rw, m, rw2), 2) * 1e25
+    op, v = _rand((R, m, n, R2), 3) * 1e-3, _rand((rv, n, rv2), 4) * 1e35
+    ref = tt.env_left_step(phi, u, op, v)
+    ref_abs = tt.env_left_step(np.abs(phi), np.abs(u), np.abs(op), np.abs(v))
+    out = torch.empty(rw2 * R2 * rv2, dtype=torch.float64, device="cuda")
+    tg.env_left_step(_dims(shape), _t(phi), _t(u), _t(op), _t(v), out, prec)
+    assert_bounded(out.cpu().numpy(), ref, ref_abs, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", [tg.MIXED_TF32, tg.MIXED_BF16])
@@ -60,9 +96,10 @@ def test_local_apply_tensor_cores(shape, prec):
     phi, psi = _rand((rw, R, rv), 9), _rand((rw2, R2, rv2), 10)
     op, x = _rand((R, m, n, R2), 11), _rand((rv, n, rv2), 12)
     ref = tt.local_apply(phi, op, psi, x)
+    ref_abs = tt.local_apply(np.abs(phi), np.abs(op), np.abs(psi), np.abs(x))
     y = torch.empty(rw * m * rw2, dtype=torch.float64, device="cuda")
     tg.local_apply(_dims(shape), _t(phi), _t(op), _t(psi), _t(x), y, prec)
-    assert _rel(y.cpu().numpy().reshape(ref.shape), ref) <= TOL[prec]
+    assert_bounded(y.cpu().numpy(), ref, ref_abs, TOL[prec])
 
 
 def test_solver_tf32_reaches_optimum():
