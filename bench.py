@@ -4,11 +4,10 @@ from host buffers, and the oracle timed on the host cores.
 
 Default workload: Max-Cut SDP, n = 2^10 vertices (d = 10 TT cores, 2 x 2
 modes), seeded Kronecker graph (ten seeded 2 x 2 0/1 patterns, unit
-weights), TT rank cap 64, target gap 1e-4. The headline form runs the
-contractions in TF32 on the tensor cores (FP32 accumulation) with the FP64
-refinement sweep, rounding and gap checks; the same instance is also solved in
-plain FP64 and in BF16, each reported with its error against the oracle's
-optimum.
+weights), TT rank cap 64, target gap 1e-4. The headline form is the plain
+FP64 solve; the same instance is also solved with TF32 and BF16 tensor-core
+contractions (FP32 accumulation, FP64 refinement sweep, rounding and gap
+checks), each form reported with its error against the oracle's optimum.
 
 The workload with Erdos-Renyi edges and weights U[0.5, 1.5] at the same size
 and cap (`--workload maxcut_d10_kron_er_cap64`) cannot reach the gap at rank
@@ -57,11 +56,13 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="maxcut_d10_kron_cap64", choices=sorted(WORKLOADS))
-    p.add_argument("--precision", default="tf32", choices=sorted(PREC))
+    p.add_argument("--precision", default="fp64", choices=sorted(PREC))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--forms", default="fp64,bf16",
+    p.add_argument("--forms", default="tf32,bf16",
                    help="other precisions solved on the same instance and reported beside the headline form")
+    p.add_argument("--form-time-limit", type=float, default=60.0,
+                   help="wall-clock seconds per solve of the other precisions (tt_sdp_options.time_limit)")
     p.add_argument("--workers", type=int, default=16, help="host threads of the batched solve")
     p.add_argument("--sequential", type=int, default=8,
                    help="batched workload: instances also solved one at a time in FP64 (0: none)")
@@ -410,9 +411,27 @@ def run_ours(a):
     # the other precisions on the same instance, each timed the same way
     forms = {a.precision: head}
     for f in [x for x in a.forms.split(",") if x and x != a.precision]:
-        o = tg.default_options(rank_cap=w["cap"], precision=PREC[f], max_iters=a.steps + 2)
-        fi, ft, fttg, _ = _solve_timed(tg, torch, wcores, o, a.steps, stream)
-        forms[f] = _form_record(fi, fttg, ft, p_star)
+        # the other precisions: one solve each through tt_sdp_solve, bounded by a
+        # wall-clock limit; time-to-gap is the device time of its iterations
+        o = tg.default_options(rank_cap=w["cap"], precision=PREC[f], max_iters=a.steps + 2,
+                               time_limit=a.form_time_limit)
+        c = tg.Context.maxcut(wcores, o)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = c.solve()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        info = c.newton_step() if r["status"] == 0 else None
+        c.close()
+        ok = r["status"] == 0
+        rec = {"time_to_gap_s": r["seconds"] if ok else None, "gap_reached": ok, "iters": r["iters"],
+               "wall_s": wall, "status": r["status"], "pobj": r["pobj"], "dobj": r["dobj"], "rel_gap": r["rel_gap"],
+               "rel_p": r["rel_p"], "rel_d": r["rel_d"], "time_limit_s": a.form_time_limit}
+        if info is not None:
+            rec.update({k: info[k] for k in ("max_rank_X", "max_rank_Z", "xz_fallbacks", "gmres_iters")})
+        if p_star is not None:
+            rec["err_vs_oracle_p_star"] = abs(r["pobj"] - p_star) / (1.0 + abs(p_star))
+        forms[f] = rec
     if "fp64" in forms:
         for f, rec in forms.items():
             if f != "fp64":

@@ -203,6 +203,45 @@ void gemm_nd(const GemmND& g, const T* A, size_t nA, const T* B, size_t nB, T* C
   check_launch("gemm_nd_kernel");
 }
 
+namespace {
+// y = alpha A x + beta y for row-major A (M x K, row stride lda): one warp
+// per row, coalesced along the row, four independent partial sums per lane.
+template <typename T>
+__global__ void gemv_rows_kernel(int M, int K, T alpha, const T* __restrict__ A, long long lda,
+                                 const T* __restrict__ x, long long incx, T beta, T* __restrict__ y,
+                                 long long incy) {
+  const int lane = threadIdx.x & 31;
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= M) return;
+  const T* a = A + row * lda;
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int k = lane;
+  for (; k + 96 < K; k += 128) {
+    s0 += a[k] * x[k * incx];
+    s1 += a[k + 32] * x[(k + 32) * incx];
+    s2 += a[k + 64] * x[(k + 64) * incx];
+    s3 += a[k + 96] * x[(k + 96) * incx];
+  }
+  for (; k < K; k += 32) s0 += a[k] * x[k * incx];
+  T s = (s0 + s1) + (s2 + s3);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row * incy] = alpha * s + (beta != T(0) ? beta * y[row * incy] : T(0));
+}
+
+// y = alpha A^T x + beta y for row-major A (K x M, row stride lda): one
+// thread per output, reading row k of A coalesced across the threads.
+template <typename T>
+__global__ void gemv_cols_kernel(int M, int K, T alpha, const T* __restrict__ A, long long lda,
+                                 const T* __restrict__ x, long long incx, T beta, T* __restrict__ y,
+                                 long long incy) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  T s = T(0);
+  for (int k = 0; k < K; ++k) s += A[(long long)k * lda + m] * x[k * incx];
+  y[m * incy] = alpha * s + (beta != T(0) ? beta * y[m * incy] : T(0));
+}
+}  // namespace
+
 template <typename T>
 void gemm_rm(bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda, long long sA,
              const T* B, int ldb, long long sB, T beta, T* C, int ldc, long long sC, int batch,
@@ -218,6 +257,22 @@ void gemm_rm(bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda
   if (!nB) nB = (size_t)(max_offset(g.N, g.bN) + max_offset(g.K, g.bK) + max_offset(g.B, g.bB)) + 1;
   if (!nC) nC = (size_t)(max_offset(g.M, g.cM) + max_offset(g.N, g.cN) + max_offset(g.B, g.cB)) + 1;
   TT_CHECK(lda >= (ta ? M : K) && ldb >= (tb ? K : N) && ldc >= N, TT_E_INTERNAL, "gemm_rm: leading dimension");
+  if (N == 1 && batch == 1 && M > 0 && K > 0) {
+    // matrix-vector product: x is column 0 of B (stride ldb, or 1 when B is
+    // given transposed), y column 0 of C (stride ldc)
+    const long long incx = tb ? 1 : ldb;
+    TT_CHECK(max_offset(g.M, g.aM) + max_offset(g.K, g.aK) < (long long)nA &&
+                 (long long)(K - 1) * incx < (long long)nB && (long long)(M - 1) * ldc < (long long)nC,
+             TT_E_INTERNAL, "gemm_rm: operand extent");
+    if (!ta) {
+      gemv_rows_kernel<T><<<ceil_div((long)M * 32, 256), 256, 0, st>>>(M, K, alpha, A, lda, B, incx, beta, C, ldc);
+    } else {
+      gemv_cols_kernel<T><<<ceil_div(M, 256), 256, 0, st>>>(M, K, alpha, A, lda, B, incx, beta, C, ldc);
+    }
+    count_launch();
+    check_launch("gemv");
+    return;
+  }
   gemm_nd<T>(g, A, nA, B, nB, C, nC, alpha, beta, st);
 }
 

@@ -6,6 +6,8 @@
 // local systems is blocked so that its trailing updates use the multi-CTA
 // strided GEMM.
 #include <cfloat>
+#include <climits>
+#include <cooperative_groups.h>
 #include <cmath>
 #include <vector>
 #include <cstring>
@@ -355,6 +357,218 @@ __global__ void __launch_bounds__(kThreads) lu_panel_kernel(int n, T* B, int j0,
   }
 }
 
+// The same panel factorisation with the panel's active rows (rows j0..n-1 of
+// its jb <= 32 columns) in shared memory for the whole panel, so the column
+// steps touch no global memory: in one CTA when they fit, else split over
+// the CTAs of a thread-block cluster (gridDim.x CTAs, launched as one
+// cluster). Per column: every CTA finds the largest entry among its rows;
+// after a cluster barrier one lane per CTA reads that CTA's candidate
+// through distributed shared memory and the warp picks the pivot (ties to
+// the smaller row, so every CTA picks the same one); the pivot row is read
+// by every CTA and the row it replaces by the pivot's owner; after a second
+// barrier the two rows are exchanged and every CTA scales its rows and
+// applies the rank-1 update. All threads of all CTAs pass the same barriers
+// (no early exit). A one-CTA launch is a cluster of one.
+constexpr int kClusterCtas = 8;
+constexpr int kPanelThreads = 256;
+constexpr int kPanelNB = 32;
+constexpr int kPanelLds = kPanelNB + 1;  // padded row stride of the shared tile
+
+template <typename T, bool kCluster, int kThr>
+__global__ void __launch_bounds__(kThr)
+    lu_panel_smem_kernel(int n, T* B, int j0, int jb, int chunk, int* ipiv) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = kCluster ? (int)cluster.block_rank() : 0;
+  const int ncta = kCluster ? (int)cluster.num_blocks() : 1;
+  // barrier over every thread of every CTA of the panel
+  auto panel_sync = [&]() {
+    if constexpr (kCluster) cluster.sync();
+    else __syncthreads();
+  };
+  // shared memory of CTA q (this CTA's own without a cluster)
+  auto remote = [&](auto* ptr, int q) {
+    if constexpr (kCluster) return cluster.map_shared_rank(ptr, q);
+    else return ptr;
+  };
+  extern __shared__ __align__(16) unsigned char panel_smem[];
+  T* tile = reinterpret_cast<T*>(panel_smem);  // [chunk][kPanelLds]
+  __shared__ T cand_val;
+  __shared__ int cand_idx;
+  __shared__ T prow[kPanelNB];
+  __shared__ T r0row[kPanelNB];
+  __shared__ T red_v[kThr / 32];
+  __shared__ int red_i[kThr / 32];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row0 = j0 + crank * chunk;  // first row of M this CTA holds
+  int nrows = n - row0;
+  nrows = nrows < 0 ? 0 : (nrows > chunk ? chunk : nrows);
+  // consecutive threads take consecutive rows of one column: coalesced loads
+  for (int e = tid; e < chunk * jb; e += kThr) {
+    const int c = e / chunk, r = e % chunk;
+    tile[r * kPanelLds + c] = r < nrows ? B[(long long)(j0 + c) * n + row0 + r] : T(0);
+  }
+  __syncthreads();
+  for (int jj = 0; jj < jb; ++jj) {
+    const int rg = j0 + jj;  // row of the diagonal entry
+    T best = T(-1);
+    int bi = INT_MAX;
+    for (int r = tid; r < nrows; r += kThr) {
+      const int g = row0 + r;
+      if (g >= rg) {
+        const T v = fabs(tile[r * kPanelLds + jj]);
+        if (v > best || (v == best && g < bi)) { best = v; bi = g; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < kThr / 32 ? red_v[lane] : T(-1);
+      bi = lane < kThr / 32 ? red_i[lane] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) { cand_val = best; cand_idx = bi; }
+    }
+    panel_sync();  // candidates of every CTA are visible
+    if (warp == 0) {
+      T bv = T(-1);
+      int bidx = INT_MAX;
+      if (lane < ncta) {
+        bv = *remote(&cand_val, lane);
+        bidx = *remote(&cand_idx, lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (oi != INT_MAX && (ov > bv || (ov == bv && oi < bidx) || bidx == INT_MAX)) { bv = ov; bidx = oi; }
+      }
+      const int p = bidx;
+      const int own_r = (rg - j0) / chunk, own_p = (p - j0) / chunk;
+      if (lane < jb) {
+        prow[lane] = remote(tile, own_p)[(p - j0 - own_p * chunk) * kPanelLds + lane];
+        if (crank == own_p && p != rg)
+          r0row[lane] = remote(tile, own_r)[(rg - j0 - own_r * chunk) * kPanelLds + lane];
+      }
+      if (lane == 0) {
+        s_piv = p;
+        if (crank == 0) ipiv[rg] = p;
+      }
+    }
+    panel_sync();  // every remote read of this column is done
+    const int p = s_piv;
+    if (warp == 0 && p != rg && lane < jb) {
+      const int own_r = (rg - j0) / chunk, own_p = (p - j0) / chunk;
+      if (crank == own_r) tile[(rg - row0) * kPanelLds + lane] = prow[lane];
+      if (crank == own_p) tile[(p - row0) * kPanelLds + lane] = r0row[lane];
+    }
+    __syncthreads();
+    const T pv = prow[jj];
+    const T inv = pv != T(0) ? T(1) / pv : T(0);
+    for (int r = tid; r < nrows; r += kThr) {
+      if (row0 + r > rg) {
+        T* tr = tile + r * kPanelLds;
+        const T l = tr[jj] * inv;
+        tr[jj] = l;
+        for (int c = jj + 1; c < jb; ++c) tr[c] -= l * prow[c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < chunk * jb; e += kThr) {
+    const int c = e / chunk, r = e % chunk;
+    if (r < nrows) B[(long long)(j0 + c) * n + row0 + r] = tile[r * kPanelLds + c];
+  }
+  // no CTA leaves while another might still address its shared memory
+  if constexpr (kCluster) cluster.sync();
+}
+
+// Row interchanges of the panel and the unit-lower triangular solve with its
+// L11 for every column of M outside the panel: one warp per column, L11 in
+// shared memory, the 32 unknowns of a column in the warp's lanes. The panel's
+// jb interchanges, applied in order, permute at most 2 jb positions; thread 0
+// composes them once per CTA (position S[k] receives the entry at src[k]),
+// and every warp then gathers and scatters its column's entries in parallel.
+template <typename T>
+__global__ void __launch_bounds__(256) lu_swap_trsm_warp_kernel(int n, T* B, int j0, int jb, const int* ipiv) {
+  __shared__ T L11[kPanelNB][kPanelNB + 1];
+  __shared__ int S[2 * kPanelNB], src[2 * kPanelNB];
+  __shared__ int s_ns;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < jb * jb; e += blockDim.x) {
+    const int t = e / jb, r = e % jb;
+    L11[r][t] = B[(long long)(j0 + t) * n + j0 + r];
+  }
+  if (warp == 0) {
+    // warp 0 composes the interchanges: S[0..jb) are the panel rows, further
+    // pivot rows are appended once (lane k watches S[jb + k]); a lookup is
+    // one ballot over the appended rows
+    if (lane < jb) { S[lane] = j0 + lane; src[lane] = j0 + lane; }
+    int ns = jb;
+    for (int jj = 0; jj < jb; ++jj) {
+      const int p = ipiv[j0 + jj];
+      if (p >= j0 + jb) {
+        const bool hit = jb + lane < ns && S[jb + lane] == p;
+        if (__ballot_sync(0xffffffffu, hit) == 0u) {
+          if (lane == 0) { S[ns] = p; src[ns] = p; }
+          ++ns;
+        }
+      }
+      __syncwarp();
+    }
+    for (int jj = 0; jj < jb; ++jj) {
+      const int p = ipiv[j0 + jj];
+      if (p == j0 + jj) continue;  // uniform across the warp
+      int kp;
+      if (p < j0 + jb) {
+        kp = p - j0;
+      } else {
+        const unsigned m = __ballot_sync(0xffffffffu, jb + lane < ns && S[jb + lane] == p);
+        kp = jb + __ffs(m) - 1;
+      }
+      if (lane == 0) {
+        const int t = src[jj];
+        src[jj] = src[kp];
+        src[kp] = t;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) s_ns = ns;
+  }
+  __syncthreads();
+  const int ns = s_ns;
+  for (int c = blockIdx.x * nw + warp; c < n - jb; c += gridDim.x * nw) {
+    const int col = c < j0 ? c : c + jb;  // skip the panel columns
+    T* cc = B + (long long)col * n;
+    const T v0 = lane < ns ? cc[src[lane]] : T(0);
+    const T v1 = lane + 32 < ns ? cc[src[lane + 32]] : T(0);
+    __syncwarp();
+    if (lane + 32 < ns) cc[S[lane + 32]] = v1;
+    if (col >= j0 + jb) {
+      // S[k] = j0 + k for k < jb: lane k holds the permuted entry of row j0 + k
+      T x = v0;
+      for (int t = 0; t + 1 < jb; ++t) {
+        const T xt = __shfl_sync(0xffffffffu, x, t);
+        if (lane > t && lane < jb) x -= L11[lane][t] * xt;
+      }
+      if (lane < ns) cc[S[lane]] = lane < jb ? x : v0;
+    } else {
+      if (lane < ns) cc[S[lane]] = v0;
+    }
+  }
+}
+
 // Row interchanges of the panel and the unit-lower triangular solve with its
 // L11 for every column of M outside the panel, one thread per column.
 template <typename T>
@@ -390,6 +604,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* B, const int* ipiv, T* b,
                                                             bool use_smem) {
   extern __shared__ __align__(16) unsigned char lu_smem[];
+  __shared__ T tri[32][33];
   T* x = use_smem ? reinterpret_cast<T*>(lu_smem) : b;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (use_smem)
@@ -400,23 +615,30 @@ __global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* B, c
     const int ib = n - i0 < 32 ? n - i0 : 32;
     for (int r = warp; r < ib; r += kWarps) {
       const T* row = B + (long long)(i0 + r) * n;
-      T s = T(0);
-      for (int t = lane; t < i0; t += 32) s += row[t] * x[t];
-      s = warp_sum(s);
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      int t = lane;
+      for (; t + 96 < i0; t += 128) {
+        s0 += row[t] * x[t];
+        s1 += row[t + 32] * x[t + 32];
+        s2 += row[t + 64] * x[t + 64];
+        s3 += row[t + 96] * x[t + 96];
+      }
+      for (; t < i0; t += 32) s0 += row[t] * x[t];
+      T s = warp_sum((s0 + s1) + (s2 + s3));
       if (lane == 0) x[i0 + r] -= s;
     }
+    // the diagonal block of U^T in shared memory, then column-oriented
+    // substitution in warp 0 with the unknowns in its lanes
+    for (int e = tid; e < ib * ib; e += kThreads) tri[e / ib][e % ib] = B[(long long)(i0 + e / ib) * n + i0 + e % ib];
     __syncthreads();
     if (warp == 0) {
-      for (int r = 0; r < ib; ++r) {
-        const T* row = B + (long long)(i0 + r) * n + i0;
-        T s = lane < r ? row[lane] * x[i0 + lane] : T(0);
-        s = warp_sum(s);
-        if (lane == 0) {
-          const T dg = row[r];
-          x[i0 + r] = dg != T(0) ? (x[i0 + r] - s) / dg : T(0);
-        }
-        __syncwarp();
+      T xv = lane < ib ? x[i0 + lane] : T(0);
+      for (int t = 0; t < ib; ++t) {
+        if (lane == t) xv = tri[t][t] != T(0) ? xv / tri[t][t] : T(0);
+        const T xt = __shfl_sync(0xffffffffu, xv, t);
+        if (lane > t && lane < ib) xv -= tri[lane][t] * xt;
       }
+      if (lane < ib) x[i0 + lane] = xv;
     }
     __syncthreads();
   }
@@ -425,20 +647,27 @@ __global__ void __launch_bounds__(kThreads) lu_apply_kernel(int n, const T* B, c
     const int i0 = i1 - 32 > 0 ? i1 - 32 : 0, ib = i1 - i0;
     for (int r = warp; r < ib; r += kWarps) {
       const T* row = B + (long long)(i0 + r) * n;
-      T s = T(0);
-      for (int t = i1 + lane; t < n; t += 32) s += row[t] * x[t];
-      s = warp_sum(s);
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      int t = i1 + lane;
+      for (; t + 96 < n; t += 128) {
+        s0 += row[t] * x[t];
+        s1 += row[t + 32] * x[t + 32];
+        s2 += row[t + 64] * x[t + 64];
+        s3 += row[t + 96] * x[t + 96];
+      }
+      for (; t < n; t += 32) s0 += row[t] * x[t];
+      T s = warp_sum((s0 + s1) + (s2 + s3));
       if (lane == 0) x[i0 + r] -= s;
     }
+    for (int e = tid; e < ib * ib; e += kThreads) tri[e / ib][e % ib] = B[(long long)(i0 + e / ib) * n + i0 + e % ib];
     __syncthreads();
     if (warp == 0) {
-      for (int r = ib - 1; r >= 0; --r) {
-        const T* row = B + (long long)(i0 + r) * n + i0;
-        T s = (lane > r && lane < ib) ? row[lane] * x[i0 + lane] : T(0);
-        s = warp_sum(s);
-        if (lane == 0) x[i0 + r] -= s;
-        __syncwarp();
+      T xv = lane < ib ? x[i0 + lane] : T(0);
+      for (int t = ib - 1; t > 0; --t) {
+        const T xt = __shfl_sync(0xffffffffu, xv, t);  // unit diagonal: x_t is final
+        if (lane < t) xv -= tri[lane][t] * xt;
       }
+      if (lane < ib) x[i0 + lane] = xv;
     }
     __syncthreads();
   }
@@ -843,17 +1072,54 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st, SvdSide side) {
   check_launch("svd_kernel");
 }
 
+// dynamic shared memory of one CTA of the cluster panel (the opt-in limit is 227 KB)
+constexpr size_t kPanelSmemMax = 220 * 1024;
+
 template <typename T>
 void lu_factor(int n, T* A, int* ipiv, cudaStream_t st) {
   if (n <= 0) return;
-  constexpr int nb = 32;
+  constexpr int nb = kPanelNB;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(lu_panel_smem_kernel<T, false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kPanelSmemMax);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(lu_panel_smem_kernel<T, true, kPanelThreads>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmemMax);
+  });
+  TT_CUDA(attr_err);
   for (int j0 = 0; j0 < n; j0 += nb) {
     int jb = n - j0 < nb ? n - j0 : nb;
-    lu_panel_kernel<T><<<1, kThreads, 0, st>>>(n, A, j0, jb, ipiv);
+    // the active rows in one CTA's shared memory when they fit, else over a
+    // cluster of kClusterCtas CTAs, else the panel streams through L2
+    const size_t row_bytes = (size_t)kPanelLds * sizeof(T);
+    if ((size_t)(n - j0) * row_bytes <= kPanelSmemMax) {
+      lu_panel_smem_kernel<T, false, 512><<<1, 512, (size_t)(n - j0) * row_bytes, st>>>(n, A, j0, jb, n - j0,
+                                                                                       ipiv);
+    } else if ((size_t)ceil_div(n - j0, kClusterCtas) * row_bytes <= kPanelSmemMax) {
+      const int chunk = ceil_div(n - j0, kClusterCtas);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kClusterCtas, 1, 1);
+      cfg.blockDim = dim3(kPanelThreads, 1, 1);
+      cfg.dynamicSmemBytes = (size_t)chunk * row_bytes;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = kClusterCtas;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      TT_CUDA(cudaLaunchKernelEx(&cfg, lu_panel_smem_kernel<T, true, kPanelThreads>, n, A, j0, jb, chunk, ipiv));
+    } else {
+      lu_panel_kernel<T><<<1, kThreads, 0, st>>>(n, A, j0, jb, ipiv);
+    }
     count_launch();
     int ncols = n - jb;
     if (ncols > 0) {
-      lu_swap_trsm_kernel<T><<<ceil_div(ncols, 128), 128, 0, st>>>(n, A, j0, jb, ipiv);
+      const int blocks = std::min(ceil_div(ncols, 8), 152 * 8);
+      lu_swap_trsm_warp_kernel<T><<<blocks, 256, 0, st>>>(n, A, j0, jb, ipiv);
       count_launch();
     }
     int rest = n - j0 - jb;
@@ -870,7 +1136,15 @@ void lu_factor(int n, T* A, int* ipiv, cudaStream_t st) {
 template <typename T>
 void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st) {
   if (n <= 0) return;
-  constexpr size_t kMaxSmem = 48 * 1024;  // default dynamic shared-memory limit
+  // the solution vector in shared memory (opt-in limit, beside the kernel's
+  // static 32 x 33 triangle) when it fits
+  constexpr size_t kMaxSmem = 160 * 1024;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(lu_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  });
+  TT_CUDA(attr_err);
   const bool use_smem = (size_t)n * sizeof(T) <= kMaxSmem;
   lu_apply_kernel<T><<<1, kThreads, use_smem ? (size_t)n * sizeof(T) : 0, st>>>(n, LU, ipiv, b, use_smem);
   count_launch();

@@ -11,6 +11,7 @@
 #include <exception>
 #include <functional>
 #include <limits>
+#include <optional>
 #include <thread>
 
 #include "contract.cuh"
@@ -384,6 +385,14 @@ double sweep_floor(int prec) {
 // FP64 sweeps that refine a direction found in a reduced precision
 constexpr int kRefineSweeps = 1;
 
+// Relative truncation tolerance of a block move in a sweep of precision
+// `prec`: the solve's tolerance, but not below the precision's noise floor.
+// Local solutions from reduced-precision contractions carry relative noise
+// of a few unit roundoffs; truncating below that level would keep noise
+// directions and let the frame ranks grow with them. The closing FP64 sweep
+// truncates at the solve's own tolerance.
+double move_tol(double tol, int prec) { return std::max(tol, sweep_floor(prec)); }
+
 // Returns the solution with the block index at the core where the last
 // sweep ended; *warm receives the same solution moved to core 0 (truncated)
 // as the warm start of the next solve.
@@ -522,6 +531,8 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
       ProfScope ps("amen.dense_solve");
       // local operators
       DBuf<double> A(n * n), AT(n * n), Ky(n * n), LZ(n * n), LX(n * n);
+      std::optional<ProfScope> ps_part;
+      ps_part.emplace("dense.local_mats");
       eA[0].local_mat(frame, k, A.get(), prec);
       eAT[0].local_mat(frame, k, AT.get(), prec);
       eK[0].local_mat(frame, k, Ky.get(), prec);
@@ -531,6 +542,8 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
       sum_local_rhs(rp, frame, k, r_p.get(), n, prec);
       sum_local_rhs(rdd, frame, k, r_d.get(), n, prec);
       sum_local_rhs(rc, frame, k, r_c.get(), n, prec);
+      ps_part.reset();
+      ps_part.emplace("dense.assemble");
       DBuf<double> K(N * N), b(N);
       dev_fill(K.get(), N * N, 0.0, st);
       // row block p: [-A, Ky, 0]
@@ -561,6 +574,8 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         dev_copy2d(b.get() + n, 1, r_t.get(), 1, n, 1, -1.0, st);
       }
       {
+        ps_part.reset();
+        ProfScope ps_lu("dense.lu");
         int corr = 0;
         const double rho = lu_solve_prec(prec, (int)N, K.get(), b.get(), kLuRefineTol, &corr);
         info->forcing = std::max(info->forcing, rho);
@@ -608,7 +623,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         svd_prec(prec_in, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
                  kSvdLeft);
         std::vector<double> hs = host_copy(S.get(), kk);
-        int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
+        int keep = truncation_rank_rel(hs, move_tol(tol, prec) / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(rows - keep, std::max(cap - keep, 0)));
         int nk = keep + std::max(extra, 0);
         DBuf<double> u((size_t)rows * nk);
@@ -653,7 +668,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         svd_prec(prec_in, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
                  kSvdRight);
         std::vector<double> hs = host_copy(S.get(), kk);
-        int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
+        int keep = truncation_rank_rel(hs, move_tol(tol, prec) / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(cols - keep, std::max(cap - keep, 0)));
         int nk = keep + std::max(extra, 0);
         DBuf<double> v((size_t)cols * nk);  // cols x nk
@@ -745,7 +760,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
       DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
       svd_thin<double>(MatView<double>{block->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st);
       std::vector<double> hs = host_copy(S.get(), kk);
-      const int keep = truncation_rank_rel(hs, tol / std::sqrt((double)d), cap);
+      const int keep = truncation_rank_rel(hs, move_tol(tol, prec) / std::sqrt((double)d), cap);
       auto fk = std::make_shared<DBuf<double>>((size_t)keep * cols);
       dev_copy(fk->get(), Vt.get(), (size_t)keep * cols, st);
       frame.c[k] = fk;

@@ -188,10 +188,44 @@ __global__ void multi_dot_kernel(const double* __restrict__ V, long long N, cons
   }
 }
 
+// part[row][blockIdx.x] = partial <V_row, w> over a fixed strided slice
+__global__ void multi_dot_split_kernel(const double* __restrict__ V, long long N, const double* __restrict__ w,
+                                       double* __restrict__ part) {
+  __shared__ double red[32];
+  const double* v = V + (long long)blockIdx.y * N;
+  double s = 0.0;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    if (i < N) s += v[i] * w[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// out[row] = sum of part[row][0..G) in index order (one warp per row)
+__global__ void sum_rows_kernel(const double* __restrict__ part, int G, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int g = 0; g < G; ++g) t += part[(long long)blockIdx.x * G + g];
+    out[blockIdx.x] = t;
+  }
+}
+
+// <a, b> by one block; with b == nullptr and n = -count: the plain sum of a[0..count)
 __global__ void dot_kernel(const double* a, const double* b, long long n, double* out) {
   __shared__ double red[32];
   double s = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
+  if (b) {
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
+  } else {
+    for (long long i = threadIdx.x; i < -n; i += blockDim.x) s += a[i];
+  }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -199,6 +233,27 @@ __global__ void dot_kernel(const double* a, const double* b, long long n, double
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
     *out = t;
+  }
+}
+
+// Partial sums of a long dot product: block b sums the strided slice
+// b, b + G, b + 2G, ... of 1024-element chunks into part[b]; a fixed
+// partition, so the result does not depend on scheduling.
+__global__ void dot_partial_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                                   double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    if (i < n) s += a[i] * b[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
   }
 }
 
@@ -250,15 +305,39 @@ void dev_scale_cols(double* a, int rows, int cols, const double* s, cudaStream_t
 }
 void dev_multi_dot(const double* V, int nvec, size_t N, const double* w, double* out, cudaStream_t st) {
   if (nvec <= 0) return;
-  multi_dot_kernel<<<nvec, 512, 0, st>>>(V, (long long)N, w, out);
-  count_launch();
+  if (N < (size_t(1) << 16) || nvec >= 152) {
+    multi_dot_kernel<<<nvec, 512, 0, st>>>(V, (long long)N, w, out);
+    count_launch();
+  } else {
+    // few long vectors: split every row over G blocks, then add the partials
+    // of each row in a fixed order
+    const long long chunks = ((long long)N + 511) / 512;
+    const int G = (int)std::min<long long>(chunks, std::max(1, 304 / nvec));
+    DBuf<double> part((size_t)nvec * G);
+    multi_dot_split_kernel<<<dim3(G, nvec), 512, 0, st>>>(V, (long long)N, w, part.get());
+    sum_rows_kernel<<<nvec, 32, 0, st>>>(part.get(), G, out);
+    count_launch();
+    count_launch();
+  }
   check_launch("multi_dot");
 }
 
 double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st) {
   DBuf<double> out(1);
-  dot_kernel<<<1, 1024, 0, st>>>(a, b, (long long)n, out.get());
-  count_launch();
+  if (n < (size_t(1) << 16)) {
+    dot_kernel<<<1, 1024, 0, st>>>(a, b, (long long)n, out.get());
+    count_launch();
+  } else {
+    // long vectors (GMRES bases of large local systems): partial sums on many
+    // SMs, then one block adds them in a fixed order
+    const long long chunks = ((long long)n + 1023) / 1024;
+    const int G = (int)(chunks < 304 ? chunks : 304);
+    DBuf<double> part((size_t)G);
+    dot_partial_kernel<<<G, 1024, 0, st>>>(a, b, (long long)n, part.get());
+    dot_kernel<<<1, 1024, 0, st>>>(part.get(), nullptr, -(long long)G, out.get());
+    count_launch();
+    count_launch();
+  }
   check_launch("dot");
   double h = 0.0;
   TT_CUDA(cudaMemcpyAsync(&h, out.get(), sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -47,10 +47,15 @@ def test_round_sdp_matches_oracle_rounding_and_shift(psd_shift, cap):
     assert math.isclose(zeta, zeta_ref, rel_tol=1e-9, abs_tol=1e-13)
     full_got, full_ref = tt.full_mat(got), tt.full_mat(ref)
     np.testing.assert_allclose(full_got, full_ref, rtol=0, atol=1e-11 * np.abs(full_ref).max())
-    # the shifted result stays within tol of the input (Corollary psdness_rounding)
-    assert np.linalg.norm(full_got - tt.full_mat(x)) <= tol * (1 + 1e-9)
+    # the result differs from the input by zeta plus the shift: within tol when
+    # the cap does not bind (Corollary psdness_rounding)
+    err = np.linalg.norm(full_got - tt.full_mat(x))
+    assert err <= zeta * (1.0 + sn) * (1 + 1e-9) + 1e-12 * tt.norm(tt.vec_tt(x))
+    if not cap:
+        assert err <= tol * (1 + 1e-9)
     if cap:
-        assert max(tt.ranks(got)) <= cap + (1 if psd_shift and zeta > 0 else 0)
+        extra = max(tt.ranks(S)) if (S is not None and zeta > 0) else 0
+        assert max(tt.ranks(got)) <= cap + extra
 
 
 def test_round_sdp_shift_keeps_psd():

@@ -44,7 +44,10 @@ def test_fp64_solve_follows_oracle_ipm_every_iteration(seed):
         it = info["iter"]
         assert math.isclose(info["pobj"], h.pobj, rel_tol=OBJ_TOL, abs_tol=1e-9), (it, info["pobj"], h.pobj)
         assert math.isclose(info["dobj"], h.dobj, rel_tol=OBJ_TOL, abs_tol=1e-9), (it, info["dobj"], h.dobj)
-        assert math.isclose(info["mu"], h.mu, rel_tol=OBJ_TOL), (it, info["mu"], h.mu)
+        # mu = <X, Z> / 2^d is a difference of nearly cancelling terms near the
+        # optimum: compared relative to the objective's scale
+        assert math.isclose(info["mu"], h.mu, rel_tol=OBJ_TOL, abs_tol=OBJ_TOL * 1e-2 * (1 + abs(h.pobj))), \
+            (it, info["mu"], h.mu)
         if ranks is not None:
             assert ranks[0] == h.ranks_X, (it, ranks[0], h.ranks_X)
             assert ranks[1] == h.ranks_Z, (it, ranks[1], h.ranks_Z)
