@@ -61,6 +61,8 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="tf32,bf16",
                    help="other precisions solved on the same instance and reported beside the headline form")
+    p.add_argument("--no-learned", dest="learned", action="store_false",
+                   help="skip the FP64 solve with the learned rank predictor")
     p.add_argument("--form-time-limit", type=float, default=60.0,
                    help="wall-clock seconds per solve of the other precisions (tt_sdp_options.time_limit)")
     p.add_argument("--workers", type=int, default=16, help="host threads of the batched solve")
@@ -362,6 +364,53 @@ def _form_record(infos, ttg, total, p_star):
     return rec
 
 
+def _learned_form(tg, torch, w, a, wcores, p_star, base):
+    """The plain FP64 solve with the learned per-bond rank predictor: the
+    network is trained on the GPU on rounding traces of two other instances of
+    the same family (seeds not used by the measured instance; untimed), then
+    the measured instance is solved with it. Reported beside the plain solve:
+    time-to-gap, the bonds rounded by the predicted-rank range finder and the
+    fallbacks to the adaptive SVD."""
+    from paper_2509_11890_gb300 import inputs
+    X, t = [], []
+    t0 = time.perf_counter()
+    for s_ in (a.seed + 1000, a.seed + 1001):
+        inst = inputs.maxcut_kron(w["d"], s_)
+        c = tg.Context.maxcut(inst["adjacency_cores"], tg.default_options(rank_cap=w["cap"], max_iters=a.steps + 2,
+                                                                           time_limit=a.form_time_limit))
+        c.set_trace(True)
+        c.solve()
+        x, y = c.trace()
+        c.close()
+        X.append(x)
+        t.append(y)
+    X, t = np.concatenate(X), np.concatenate(t)
+    pred = tg.RankPredictor(seed=7)
+    loss = pred.train(X, t, epochs=300, batch=64, lr=2e-3, seed=1)
+    train_s = time.perf_counter() - t0
+    o = tg.default_options(rank_cap=w["cap"], precision=0, max_iters=a.steps + 2, time_limit=a.form_time_limit)
+    c = tg.Context.maxcut(wcores, o)
+    c.set_rank_predictor(pred)
+    torch.cuda.synchronize()
+    r = c.solve()
+    torch.cuda.synchronize()
+    info = c.newton_step() if r["status"] == 0 else None
+    c.close()
+    ok = r["status"] == 0
+    rec = {"time_to_gap_s": r["seconds"] if ok else None, "gap_reached": ok, "iters": r["iters"],
+           "pobj": r["pobj"], "dobj": r["dobj"], "rel_gap": r["rel_gap"], "rel_p": r["rel_p"], "rel_d": r["rel_d"],
+           "trace_rows": int(len(t)), "train_loss": loss, "trace_and_train_s": train_s}
+    if info is not None:
+        used, fb = info["pred_used"], info["pred_fallbacks"]
+        rec.update({"bonds_by_range_finder": used, "fallbacks": fb,
+                    "fallback_rate": fb / (used + fb) if used + fb else None})
+    if p_star is not None:
+        rec["err_vs_oracle_p_star"] = abs(r["pobj"] - p_star) / (1.0 + abs(p_star))
+    if ok and base.get("time_to_gap_s"):
+        rec["speedup_vs_plain_fp64"] = base["time_to_gap_s"] / r["seconds"]
+    return rec
+
+
 def run_ours(a):
     import torch
 
@@ -405,6 +454,7 @@ def run_ours(a):
         torch.distributed.barrier()
     cflops, csec = tg.contraction_stats()
     tflops, tsec, tlaunch = tg.tc_stats()
+    lflops, lsec, lcalls = tg.lu_stats()
     reached = ttg is not None
     ttg_all, total = max_over_ranks([ttg if reached else float("inf"), total], device="cuda")
     head = _form_record(infos, ttg, total, p_star)
@@ -417,21 +467,33 @@ def run_ours(a):
                                time_limit=a.form_time_limit)
         c = tg.Context.maxcut(wcores, o)
         torch.cuda.synchronize()
+        tg.contraction_stats_reset()
         t0 = time.perf_counter()
         r = c.solve()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        fcf, fcs = tg.contraction_stats()
+        ftf, fts, ftl = tg.tc_stats()
+        flf, fls, flc = tg.lu_stats()
         info = c.newton_step() if r["status"] == 0 else None
         c.close()
         ok = r["status"] == 0
         rec = {"time_to_gap_s": r["seconds"] if ok else None, "gap_reached": ok, "iters": r["iters"],
                "wall_s": wall, "status": r["status"], "pobj": r["pobj"], "dobj": r["dobj"], "rel_gap": r["rel_gap"],
-               "rel_p": r["rel_p"], "rel_d": r["rel_d"], "time_limit_s": a.form_time_limit}
+               "rel_p": r["rel_p"], "rel_d": r["rel_d"], "time_limit_s": a.form_time_limit,
+               "contraction_tflops": fcf / fcs / 1e12 if fcs > 0 else 0.0,
+               "tc_gemm": {"launches": ftl, "tflops": ftf / fts / 1e12 if fts > 0 else 0.0,
+                           "us_per_launch": fts / max(ftl, 1) * 1e6,
+                           "frac_of_peak": (ftf / fts / 1e12) / (_peaks()[0]["bf16_tflops_sustained"] *
+                                                                 (0.5 if f == "tf32" else 1.0)) if fts > 0 else 0.0},
+               "lu": {"systems": flc, "tflops": flf / fls / 1e12 if fls > 0 else 0.0, "seconds": fls}}
         if info is not None:
             rec.update({k: info[k] for k in ("max_rank_X", "max_rank_Z", "xz_fallbacks", "gmres_iters")})
         if p_star is not None:
             rec["err_vs_oracle_p_star"] = abs(r["pobj"] - p_star) / (1.0 + abs(p_star))
         forms[f] = rec
+    if a.learned and w["kind"] == "maxcut":
+        forms["fp64_learned"] = _learned_form(tg, torch, w, a, wcores, p_star, head)
     if "fp64" in forms:
         for f, rec in forms.items():
             if f != "fp64":
@@ -470,7 +532,14 @@ def run_ours(a):
         bound, peak, punit = "tensor", peaks["bf16_tflops_sustained"] * ratio, "TFLOP/s"
         peak_note = f"{peak_kind} bf16 sustained x {ratio} (nominal dtype ratio)"
     contraction_tflops = cflops / csec / 1e12 if csec > 0 else 0.0
-    if bound == "tensor":
+    lu_tflops = lflops / lsec / 1e12 if lsec > 0 else 0.0
+    if lsec > csec and a.precision == "fp64":
+        # the dense local LU solves take most of the FP64 iteration
+        achieved = lu_tflops
+        kernel = (f"dense local LU solves (shared-memory panel, warp TRSM, trailing GEMM, triangular solves): "
+                  f"{lcalls} systems, {lflops / max(lcalls, 1) / 1e9:.4f} GFLOP and "
+                  f"{lsec / max(lcalls, 1) * 1e3:.3f} ms per system")
+    elif bound == "tensor":
         # the tensor-core kernel: tcgen05 GEMM of the contraction stages
         achieved = tflops / tsec / 1e12 if tsec > 0 else 0.0
         kernel = (f"tc_gemm_kernel (tcgen05 {a.precision.upper()} GEMM of the contractions): "
@@ -491,6 +560,9 @@ def run_ours(a):
         "oracle_p_star": p_star,
         "contraction_tflops": contraction_tflops,
         "contraction_share": csec / total if total > 0 else None,
+        "lu_tflops": lu_tflops,
+        "lu_share": lsec / total if total > 0 else None,
+        "lu_systems": lcalls,
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
                      "frac": achieved / peak if peak else None, "traffic": None, "peak_source": peak_note,
                      "kernel": kernel},

@@ -403,34 +403,37 @@ void tt_sdp_destroy(tt_sdp_ctx* ctx);
  * sketch product runs on the TF32 tensor cores. The exact FP64 truncation
  * error of the sketched bond is checked against the bond tolerance; when it
  * exceeds it (or the rank cap would bind) the bond falls back to the
- * adaptive SVD, which has the final word. Network: 9 features -> 64 -> 64 -> 64
+ * adaptive SVD, which has the final word. Network: 10 features -> 64 -> 64 -> 64
  * -> 1, tanh hidden layers, sigmoid output = rank / cap, trained on the GPU
  * (mean squared error, Adam) by the library's own kernels. Features of a
  * bond: one-hot variable (X, Y, T, Z), bond position k/(d-2), log10(mu)/10,
- * input rank / cap, previous rank of that bond / cap, iteration / max_iters.
+ * input rank / cap, previous rank of that bond / cap, iteration / max_iters,
+ * and the singular-value decay seen at that bond in the variable's previous
+ * rounding (log10(sigma_kept_last / sigma_1) / 16, 0 before the first), which
+ * costs no extra decomposition.
  * All arrays below are HOST arrays.
  * ------------------------------------------------------------------------- */
 typedef struct tt_rankpred tt_rankpred;
 
-/* Number of float parameters (9089). */
+/* Number of float parameters (9153). */
 int32_t tt_rankpred_param_count(void);
 /* Xavier-initialised network from the SplitMix64 stream `seed`. */
 tt_status tt_rankpred_create(uint64_t seed, tt_rankpred** out);
 void tt_rankpred_destroy(tt_rankpred* p);
 tt_status tt_rankpred_get_params(const tt_rankpred* p, float* out);
 tt_status tt_rankpred_set_params(tt_rankpred* p, const float* in);
-/* Mean squared error on (X: n x 9, t: n) and its gradient (param_count floats). */
+/* Mean squared error on (X: n x 10, t: n) and its gradient (param_count floats). */
 tt_status tt_rankpred_grad(tt_rankpred* p, const float* X, const float* t, int32_t n, float* grad, float* loss);
 /* Adam (beta 0.9 / 0.999) on shuffled mini-batches; *loss = final full-data loss. */
 tt_status tt_rankpred_train(tt_rankpred* p, const float* X, const float* t, int32_t n, int32_t epochs,
                             int32_t batch, float lr, uint64_t seed, float* loss);
-/* y (n values in (0, 1)) for the feature rows X (n x 9). */
+/* y (n values in (0, 1)) for the feature rows X (n x 10). */
 tt_status tt_rankpred_predict(const tt_rankpred* p, const float* X, int32_t n, float* y);
 /* Attach a copy of the predictor to a context (NULL detaches). */
 tt_status tt_sdp_set_rank_predictor(tt_sdp_ctx* ctx, const tt_rankpred* p);
 /* Record (features, adaptive-SVD rank / cap) of every bond rounded by the adaptive SVD. */
 tt_status tt_sdp_set_trace(tt_sdp_ctx* ctx, int32_t on);
-/* Copy the recorded trace: X (n x 9 floats) and t (n floats); with X == NULL only *n is set. */
+/* Copy the recorded trace: X (n x 10 floats) and t (n floats); with X == NULL only *n is set. */
 tt_status tt_sdp_get_trace(tt_sdp_ctx* ctx, float* X, float* t, size_t* n);
 
 /* ---------------------------------------------------------------------------
@@ -449,6 +452,12 @@ void tt_contraction_stats_reset(void);
  * reset: algorithmic flops (2 M N K with the unpadded K), device seconds from
  * CUDA events around each launch, and the launch count. */
 void tt_tc_stats(double* flops, double* seconds, uint64_t* launches);
+/* Dense local solves of the AMEn sweeps (LU with partial pivoting and its
+ * triangular solves, FP64, or FP32 factors with FP64 refinement) since the
+ * last reset: algorithmic flops (2 N^3 / 3 per factorisation plus 2 N^2 per
+ * triangular-solve pair), device seconds from CUDA events and the number of
+ * local systems. Reset with tt_contraction_stats_reset. */
+void tt_lu_stats(double* flops, double* seconds, uint64_t* calls);
 /* Per-phase host wall time accumulated while the environment variable
  * TTSDP_PROFILE=1 is set (each phase then synchronises the stream): one
  * "name seconds" line per phase, written NUL-terminated into buf (at most cap

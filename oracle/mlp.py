@@ -3,18 +3,18 @@
 TEST INFRASTRUCTURE ONLY. Nothing in the product path may import this module.
 
 The predictor is not part of the paper: it is the build's learned rank
-choice for TT rounding. Network: 9 features -> 64 -> 64 -> 64 -> 1 with tanh
+choice for TT rounding. Network: 10 features -> 64 -> 64 -> 64 -> 1 with tanh
 hidden activations and a sigmoid output, trained on the mean squared error
 against the rank the adaptive SVD chose, divided by the rank cap.
 
-Parameters are one flat vector in the order W1 (64 x 9, row-major), b1 (64),
+Parameters are one flat vector in the order W1 (64 x 10, row-major), b1 (64),
 W2 (64 x 64), b2 (64), W3 (64 x 64), b3 (64), w4 (64), b4 (1).
 """
 from __future__ import annotations
 
 import numpy as np
 
-NIN, NH = 9, 64
+NIN, NH = 10, 64
 SIZES = [(NH, NIN), (NH,), (NH, NH), (NH,), (NH, NH), (NH,), (NH,), (1,)]
 NPARAM = int(sum(np.prod(s) for s in SIZES))
 

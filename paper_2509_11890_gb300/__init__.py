@@ -384,7 +384,7 @@ class Context:
     def trace(self):
         n = ctypes.c_size_t(0)
         _check(lib().tt_sdp_get_trace(self._h, None, None, ctypes.byref(n)), "tt_sdp_get_trace")
-        X = np.empty((n.value, 9), dtype=np.float32)
+        X = np.empty((n.value, 10), dtype=np.float32)
         t = np.empty(n.value, dtype=np.float32)
         if n.value:
             _check(lib().tt_sdp_get_trace(self._h, X.ctypes.data, t.ctypes.data, ctypes.byref(n)), "tt_sdp_get_trace")
@@ -541,3 +541,10 @@ def profile_report() -> dict:
         k, v = ln.split()
         out[k] = float(v)
     return out
+
+
+def lu_stats():
+    """(flops, seconds, systems) of the dense local LU solves since the last reset."""
+    f, s, n = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_uint64(0)
+    lib().tt_lu_stats(ctypes.byref(f), ctypes.byref(s), ctypes.byref(n))
+    return f.value, s.value, n.value

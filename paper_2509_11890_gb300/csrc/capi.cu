@@ -202,6 +202,18 @@ void tt_tc_stats(double* flops, double* seconds, uint64_t* launches) {
   }
 }
 
+void tt_lu_stats(double* flops, double* seconds, uint64_t* calls) {
+  try {
+    unsigned long long c = 0;
+    stats_read(flops, seconds, 2, &c);
+    if (calls) *calls = c;
+  } catch (...) {
+    if (flops) *flops = 0;
+    if (seconds) *seconds = 0;
+    if (calls) *calls = 0;
+  }
+}
+
 size_t tt_core_count(int32_t d, const int32_t* ranks, int32_t m, int32_t n) {
   if (d <= 0 || !ranks) return 0;
   size_t s = 0;

@@ -424,20 +424,20 @@ struct Stats {
 };
 struct Registry {
   std::mutex mu;
-  std::vector<std::shared_ptr<Stats>> all[2];
+  std::vector<std::shared_ptr<Stats>> all[kStatKeys];
 };
 Registry& registry() {
   static Registry r;
   return r;
 }
 Stats& stats(int key) {
-  static thread_local std::shared_ptr<Stats> mine[2];
-  std::shared_ptr<Stats>& m = mine[key & 1];
+  static thread_local std::shared_ptr<Stats> mine[kStatKeys];
+  std::shared_ptr<Stats>& m = mine[key % kStatKeys];
   if (!m) {
     m = std::make_shared<Stats>();
     Registry& r = registry();
     std::lock_guard<std::mutex> lk(r.mu);
-    r.all[key & 1].push_back(m);
+    r.all[key % kStatKeys].push_back(m);
   }
   return *m;
 }
@@ -487,7 +487,7 @@ void stats_read(double* flops, double* seconds, int key, unsigned long long* cal
   std::lock_guard<std::mutex> lk(r.mu);
   double f = 0.0, sec = 0.0;
   unsigned long long c = 0;
-  for (auto& sp : r.all[key & 1]) {
+  for (auto& sp : r.all[key % kStatKeys]) {
     std::lock_guard<std::mutex> lk2(sp->mu);
     resolve(*sp);
     f += sp->flops;
@@ -502,7 +502,7 @@ void stats_read(double* flops, double* seconds, int key, unsigned long long* cal
 void stats_reset() {
   Registry& r = registry();
   std::lock_guard<std::mutex> lk(r.mu);
-  for (int key = 0; key < 2; ++key)
+  for (int key = 0; key < kStatKeys; ++key)
     for (auto& sp : r.all[key]) {
       std::lock_guard<std::mutex> lk2(sp->mu);
       resolve(*sp);

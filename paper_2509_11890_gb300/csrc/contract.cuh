@@ -29,8 +29,10 @@ void local_matrix(const CDims& d, const double* phi, const double* op, const dou
 void to_f32(const double* a, float* b, size_t n, cudaStream_t st);
 void to_f64(const float* a, double* b, size_t n, cudaStream_t st);
 
-// Contraction statistics (device time via CUDA events and algorithmic flops).
-// key 0: whole contraction calls; key 1: tensor-core GEMM launches.
+// Statistics of timed work (device time via CUDA events and algorithmic
+// flops). key 0: whole contraction calls; key 1: tensor-core GEMM launches;
+// key 2: LU factorisations and solves of the dense local systems.
+constexpr int kStatKeys = 3;
 void stats_begin(cudaStream_t st, int key = 0);
 void stats_end(cudaStream_t st, double flops, int key = 0);
 void stats_read(double* flops, double* seconds, int key = 0, unsigned long long* calls = nullptr);

@@ -11,7 +11,7 @@
 
 namespace ttsdp {
 
-constexpr int kPredIn = 9, kPredHidden = 64;
+constexpr int kPredIn = 10, kPredHidden = 64;
 constexpr int kPredParams = kPredHidden * kPredIn + kPredHidden + 2 * (kPredHidden * kPredHidden + kPredHidden) +
                             kPredHidden + 1;
 

@@ -222,6 +222,9 @@ constexpr double kLuRefineTol = 1e-10;
 // ftol ||b|| or five corrections have run.
 double lu_solve_prec(int prec, int N, double* K, double* b, double ftol, int* corrections) {
   cudaStream_t st = cur_stream();
+  // timed as one unit: factorisation 2 N^3 / 3 flops, every solve 2 N^2
+  stats_begin(st, 2);
+  int nsolve = 0;
   const size_t nn = (size_t)N * N;
   const double bnorm = dev_norm(b, N);
   DBuf<double> x(N), r(N);
@@ -236,6 +239,7 @@ double lu_solve_prec(int prec, int N, double* K, double* b, double ftol, int* co
     dev_copy(Kc.get(), K, nn, st);
     dev_copy(x.get(), b, N, st);
     lu_solve<double>(N, Kc.get(), x.get(), st);
+    ++nsolve;
     rho = residual();
   } else {
     DBuf<float> kf(nn), rf(N);
@@ -248,6 +252,7 @@ double lu_solve_prec(int prec, int N, double* K, double* b, double ftol, int* co
     for (int it = 0; it < 5; ++it) {
       to_f32(r.get(), rf.get(), N, st);
       lu_solve_factored<float>(N, kf.get(), ipiv.get(), rf.get(), st);
+      ++nsolve;
       to_f64(rf.get(), dx.get(), N, st);
       dev_axpy(x.get(), dx.get(), N, 1.0, st);
       if (corrections && it > 0) ++*corrections;
@@ -256,6 +261,7 @@ double lu_solve_prec(int prec, int N, double* K, double* b, double ftol, int* co
     }
   }
   dev_copy(b, x.get(), N, st);
+  stats_end(st, 2.0 / 3.0 * (double)N * N * N + 2.0 * (double)N * N * nsolve, 2);
   return rho;
 }
 
@@ -1354,11 +1360,14 @@ DTT Solver::round_psd(const DTT& Mx, double delta, const DTT* shift, int var_id)
   double sn = shift ? tt_norm(vecv(*shift)) : 0.0;
   std::vector<int>& prev = prev_[var_id & 3];
   if ((int)prev.size() != p_.d + 1) prev.assign(p_.d + 1, 0);
+  std::vector<float>& decay = decay_[var_id & 3];
+  if ((int)decay.size() != p_.d + 1) decay.assign(p_.d + 1, 0.f);
   RoundHook hook;
   hook.var_id = var_id;
   hook.mu = mu_now_;
   hook.iter_frac = (double)it_ / (double)std::max(o_.max_iters, 1);
   hook.prev = &prev;
+  hook.decay = &decay;
   hook.pred = pred_.get();
   hook.rnd = &rnd_;
   if (trace_) {

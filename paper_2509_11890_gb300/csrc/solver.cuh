@@ -137,6 +137,7 @@ class Solver {
   bool trace_ = false;
   std::vector<float> trace_x_, trace_y_;
   std::vector<int> prev_[4];
+  std::vector<float> decay_[4];
   long long pred_used_ = 0, pred_fallbacks_ = 0;
   double forcing_it_ = 0.0;
   long long corrections_ = 0;

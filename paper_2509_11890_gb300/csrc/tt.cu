@@ -678,8 +678,9 @@ int truncation_rank(const std::vector<double>& s, double thr, int cap) {
   return keep;
 }
 
-// Features of the learned rank predictor for bond k (9 values): one-hot variable,
-// bond position, log10(mu) / 10, input rank / cap, previous rank / cap, iteration fraction.
+// Features of the learned rank predictor for bond k (10 values): one-hot variable,
+// bond position, log10(mu) / 10, input rank / cap, previous rank / cap, iteration
+// fraction, and the singular-value decay of this bond at the previous rounding.
 static void bond_features(const RoundHook& h, int k, int d, int in_rank, int cap, float* f) {
   for (int i = 0; i < 4; ++i) f[i] = (h.var_id == i) ? 1.f : 0.f;
   f[4] = d > 2 ? (float)k / (float)(d - 2) : 0.f;
@@ -688,6 +689,14 @@ static void bond_features(const RoundHook& h, int k, int d, int in_rank, int cap
   const int prev = h.prev && (int)h.prev->size() > k + 1 ? (*h.prev)[k + 1] : 0;
   f[7] = (float)prev / (float)std::max(cap, 1);
   f[8] = (float)h.iter_frac;
+  f[9] = h.decay && (int)h.decay->size() > k + 1 ? (*h.decay)[k + 1] : 0.f;
+}
+
+// log10(sigma_keep / sigma_1) / 16 of a bond's spectrum at its kept rank
+static float spectrum_decay(const std::vector<double>& s, int keep) {
+  if (s.empty() || s[0] <= 0.0 || keep < 1) return 0.f;
+  const double last = s[(size_t)std::min<int>(keep, (int)s.size()) - 1];
+  return (float)(std::log10(std::max(last, 1e-300) / s[0]) / 16.0);
 }
 
 // One bond by the fixed-rank randomised range finder (Halko, Martinsson & Tropp
@@ -695,7 +704,8 @@ static void bond_features(const RoundHook& h, int k, int d, int in_rank, int cap
 // of the small B in FP64. The exact FP64 truncation error ||A||^2 - sum of the
 // kept sigma^2 must stay within the bond threshold, otherwise the caller falls
 // back to the adaptive SVD. Returns the kept rank (0: rejected).
-static int round_bond_sketch(DTT& t, int k, int l, double thr, int cap, Counter& rnd, double* err2) {
+static int round_bond_sketch(DTT& t, int k, int l, double thr, int cap, Counter& rnd, double* err2,
+                             float* decay) {
   cudaStream_t st = cur_stream();
   const int M = t.m * t.n, r = t.r[k], r2 = t.r[k + 1], rows = r * M;
   const double* A = t.core(k);
@@ -742,6 +752,7 @@ static int round_bond_sketch(DTT& t, int k, int l, double thr, int cap, Counter&
   t.c[k + 1] = xc;
   t.r[k + 1] = keep;
   *err2 = tail;
+  *decay = spectrum_decay(hs, keep);
   return keep;
 }
 
@@ -773,11 +784,13 @@ std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* 
       const int l = std::min(rh + 4, kk);
       if (l < kk) {
         double e2 = 0.0;
-        const int kept = round_bond_sketch(t, k, l, thr, cap, *hook->rnd, &e2);
+        float dec = 0.f;
+        const int kept = round_bond_sketch(t, k, l, thr, cap, *hook->rnd, &e2, &dec);
         if (kept > 0) {
           zeta2 += e2;
           ++hook->used;
           if (hook->prev && (int)hook->prev->size() > k + 1) (*hook->prev)[k + 1] = kept;
+          if (hook->decay && (int)hook->decay->size() > k + 1) (*hook->decay)[k + 1] = dec;
           continue;
         }
         ++hook->fallbacks;
@@ -800,6 +813,7 @@ std::pair<DTT, double> tt_round(const DTT& a, double delta, int cap, RoundHook* 
       hook->trace_y->push_back((float)keep / (float)std::max(cap, 1));
     }
     if (hook && hook->prev && (int)hook->prev->size() > k + 1) (*hook->prev)[k + 1] = keep;
+    if (hook && hook->decay && (int)hook->decay->size() > k + 1) (*hook->decay)[k + 1] = spectrum_decay(hs, keep);
     auto nc = std::make_shared<DBuf<double>>((size_t)rows * keep);
     dev_copy2d(nc->get(), keep, U.get(), kk, rows, keep, 1.0, st);
     // next core <- diag(S[:keep]) Vt[:keep] core_{k+1}, with diag(S) Vt = U^T A

@@ -73,6 +73,7 @@ struct RoundHook {
   int var_id = 0;                      // 0 X, 1 Y, 2 T, 3 Z
   double mu = 1.0, iter_frac = 0.0;
   std::vector<int>* prev = nullptr;    // previous rounded ranks of this variable (d + 1), updated
+  std::vector<float>* decay = nullptr; // singular-value decay per bond at the previous rounding (d + 1), updated
   const RankPredictor* pred = nullptr; // when set: fixed-rank randomised range finder per bond
   std::vector<float>* trace_x = nullptr;
   std::vector<float>* trace_y = nullptr;

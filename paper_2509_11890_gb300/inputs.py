@@ -261,6 +261,29 @@ def cc_signed(d: int, seed: int, flip_frac: float = 0.05) -> dict:
     }
 
 
+def cc_signed_sub(d_full: int, d_sub: int, seed: int, flip_frac: float = 0.05) -> dict:
+    """Principal sub-instance of the correlation-clustering instance of order
+    d_full: the rows and columns whose d_full - d_sub most significant binary
+    digits are 0 (the leading 2^d_sub x 2^d_sub block), a complete signed
+    graph of order d_sub in the same vertex numbering."""
+    full = cc_signed(d_full, seed, flip_frac)
+    n = 2**d_sub
+    w = full["weights"][:n, :n].copy()
+    adj = np.ones((n, n), dtype=np.int8)
+    np.fill_diagonal(adj, 0)
+    return {
+        "kind": "cc",
+        "d": d_sub,
+        "d_full": d_full,
+        "seed": seed,
+        "adjacency": adj,
+        "weights": w,
+        "c_plus": np.where(w > 0, w, 0.0),
+        "c_minus": np.where(w < 0, -w, 0.0),
+        "adjacency_cores": None,
+    }
+
+
 def batch_maxcut(count: int, seed: int, d_lo: int = 6, d_hi: int = 11) -> list[dict]:
     """`count` Kronecker Max-Cut instances with d ~ U{d_lo..d_hi}."""
     g = rng(seed, _STREAM_BATCH)

@@ -69,3 +69,16 @@ def test_batch_orders_and_reproducibility():
     assert all(6 <= i["d"] <= 11 for i in b1)
     for x, y in zip(b1, b2):
         np.testing.assert_array_equal(x["adjacency"], y["adjacency"])
+
+
+def test_cc_sub_instance_is_the_leading_block_of_the_full_instance():
+    full = inputs.cc_signed(9, 3)
+    sub = inputs.cc_signed_sub(9, 6, 3)
+    n = 2 ** 6
+    np.testing.assert_array_equal(sub["weights"], full["weights"][:n, :n])
+    w = sub["weights"]
+    assert w.shape == (n, n) and np.array_equal(w, w.T) and np.all(np.diag(w) == 0)
+    off = w[~np.eye(n, dtype=bool)]
+    assert set(np.unique(off)) <= {-1.0, 1.0}
+    np.testing.assert_array_equal(sub["c_plus"] - sub["c_minus"], w)
+    assert sub["adjacency"].sum() == n * (n - 1)
