@@ -236,6 +236,22 @@ typedef struct {
                               progress is abandoned at its next core step, the
                               context keeps the last completed iterate and the solve
                               returns TT_E_NO_CONVERGENCE                          */
+  int32_t combined_multipliers; /* 1 (default): with inequalities whose non-idle mask
+                              I - K_T is disjoint from that of Y, I - K_Y, and all of
+                              A_eq, A_ineq, K_Y, K_T diagonal, dY and dT are one block
+                              dLambda of the AMEn solve (Section 3.5, "Combined
+                              Multiplier Storage"); 0: separate blocks            */
+  double finish_tol;       /* finishing phase (Section 3.5, "Relaxing the Positive
+                              Definiteness Barrier"), 0 (default): off. When > 0, once
+                              the relative criteria hold the solve goes on until
+                              ||R_p||_F, ||R_d||_F and |<X,Z> + <vec T, s>| are all
+                              below finish_tol, with step lengths for the relaxed
+                              cone M + nu I >= 0 and updates kept only when they
+                              lower the merit ||R_p|| + ||R_d|| + |gap| while the
+                              relative criteria still hold; a rejected update keeps
+                              the iterate and multiplies nu by 10, up to nu_max,
+                              after which the phase ends                          */
+  double nu0, nu_max;      /* first and largest relaxation nu (1e-6, 1e-3)            */
 } tt_sdp_options;
 
 typedef struct tt_sdp_ctx tt_sdp_ctx;
@@ -265,6 +281,11 @@ typedef struct {
    * direction so far, because an AMEn solve missed its tolerance within the
    * sweep budget or the admissible step was below 1e-3.                      */
   int64_t xz_fallbacks;
+  /* Finishing phase (Section 3.5): 1 when this iteration belonged to it, then
+   * whether its update was kept, the relaxation nu of its step lengths and the
+   * merit of the iterate it started from.                                    */
+  int32_t finishing, accepted;
+  double nu, merit;
 } tt_sdp_iter_info;
 
 typedef struct {

@@ -89,6 +89,24 @@ def op_identity(d: int) -> list:
     return tt.identity_op(d, 4)
 
 
+def op_diagonal(op: list) -> list:
+    """The diagonal of an operator that is diag_TT of a vector: that vector's
+    cores, core [p][i][q] = op[p][i][i][q] (the off-diagonal mode entries must be 0)."""
+    out = []
+    for c in op:
+        m = c.shape[1]
+        off = c.copy()
+        for i in range(m):
+            off[:, i, i, :] = 0.0
+        assert np.abs(off).max() <= 1e-14 * max(np.abs(c).max(), 1.0), "operator is not diagonal"
+        out.append(np.ascontiguousarray(np.stack([c[:, i, i, :] for i in range(m)], axis=1)))
+    return out
+
+
+def _ones4(d: int) -> list:
+    return [np.ones((1, 4, 1)) for _ in range(d)]
+
+
 # ----------------------------------------------------------------------------
 # environments of one (frame, operator, vector) triple
 # ----------------------------------------------------------------------------
@@ -148,6 +166,7 @@ class NewtonData:
     A_ineqT: list | None = None
     rhs_t: list | None = None
     sgn: float = 1.0
+    masks: tuple | None = None   # (P_Y, P_T) diagonals when dY, dT share one block dLambda
 
     @property
     def nblk(self) -> int:
@@ -553,6 +572,13 @@ class Options:
     eig_sweeps: int = 4
     eig_two_site: bool = True   # two-site DMRG sweeps (Section 3.4); False: one-site ALS
     max_retries: int = 4        # damp-and-retry of an update that left the cone (Section 3.5)
+    combined_multipliers: bool = True  # one block dLambda for dY and dT when their masks are disjoint (Section 3.5)
+    # finishing phase (Section 3.5, "Relaxing the Positive Definiteness Barrier"): after
+    # the relative criteria hold, iterate on with step lengths for M + nu I >= 0 until
+    # ||R_p||_F, ||R_d||_F and the complementarity are below finish_tol (0: off)
+    finish_tol: float = 0.0
+    nu0: float = 1e-6
+    nu_max: float = 1e-3
     fallback_step: float = 1e-3  # AHO -> XZ fallback below this step length (Section 3.5)
 
 
@@ -568,6 +594,10 @@ class IterInfo:
     alpha_p: float = 0.0
     alpha_d: float = 0.0
     direction: str = ""
+    finishing: bool = False   # an iteration of the finishing phase
+    accepted: bool = True     # its update reduced the merit (finishing phase)
+    nu: float = 0.0           # barrier relaxation of its step lengths
+    merit: float = 0.0        # merit of the iterate it started from (finishing phase)
     ranks_X: list = field(default_factory=list)
     ranks_Z: list = field(default_factory=list)
     ranks_W: list = field(default_factory=list)   # frame kept as the next solve's warm start
@@ -628,6 +658,8 @@ class TTIPM:
         self.history = []
         self.prev = None      # last update: iterate, direction, step lengths, rounding tolerances
         self.retries = 0
+        self.nu = 0.0            # relaxation M + nu I >= 0 of the step lengths (finishing phase)
+        self.finish_done = False
         self.fallbacks = 0
 
     # --- residuals and measures (Section 3.3, Section 3.5) ---
@@ -721,13 +753,52 @@ class TTIPM:
                 data.rhs_t.append((1.0, tt.diag_tt(tt.vec_tt(dTa)), dsa))
         return data
 
+    def combine_multipliers(self, data: NewtonData) -> NewtonData:
+        """Combined multiplier storage (Section 3.5, "Combined Multiplier Storage").
+
+        With the non-idle masks P_Y = I - K_Y and P_T = I - K_T disjoint, dY and
+        dT are kept in one block dLambda (dY = P_Y dLambda, dT = P_T dLambda).
+        The multiplier rows become P_Y (p-row) + P_T (t-row):
+            (-P_Y A_eq + sgn P_T T A_ineq) dX + (P_Y K_Y P_Y + P_T (D_ineq + K_T) P_T) dLambda
+                = -(P_Y R_p + P_T R_t),
+        the multiplier column of the dZ equation becomes A_eq^T P_Y - sgn A_ineq^T P_T,
+        and the dX and dZ equations are otherwise unchanged. All operators here
+        are diag_TT of vectors, so products are Hadamard products of their
+        diagonals, and for 0/1 masks P D P = P D. Returns `data` itself when the
+        masks overlap."""
+        p, d = self.p, self.d
+        one = _ones4(d)
+        pY = tt.add(one, op_diagonal(p.K_y), 1.0, -1.0)
+        pT = tt.add(one, op_diagonal(p.K_t), 1.0, -1.0)
+        if abs(tt.inner(pY, pT)) > 1e-9:
+            return data
+        sg = data.sgn
+        a_eq, a_in = op_diagonal(p.A_eq), op_diagonal(p.A_ineq)
+        row = tt.add(tt.hadamard(pY, a_eq), tt.hadamard(pT, op_diagonal(data.TA)), 1.0, -sg)
+        dk = op_diagonal(data.D_K[0])
+        for o in data.D_K[1:]:
+            dk = tt.add(dk, op_diagonal(o))
+        lam = tt.add(tt.hadamard(pY, op_diagonal(p.K_y)), tt.hadamard(pT, dk))
+        col = tt.add(tt.hadamard(pY, a_eq), tt.hadamard(pT, a_in), 1.0, -sg)
+        rhs = [(c, tt.diag_tt(tt.hadamard(pY, op_diagonal(o))), v) for c, o, v in data.rhs_p]
+        rhs += [(c, tt.diag_tt(tt.hadamard(pT, op_diagonal(o))), v) for c, o, v in data.rhs_t]
+        return NewtonData(A_eq=tt.diag_tt(row), A_eqT=tt.diag_tt(col), K_y=tt.diag_tt(lam), LZ=data.LZ, LX=data.LX,
+                          rhs_p=rhs, rhs_d=data.rhs_d, rhs_c=data.rhs_c, sgn=sg, masks=(pY, pT))
+
     def direction(self, direction, sigma_mu, corr, zero_p, zero_d):
         data = self.newton_data(direction, sigma_mu, corr, zero_p, zero_d)
+        if data.TA is not None and self.o.combined_multipliers:
+            data = self.combine_multipliers(data)
         w, warm, info = amen_solve(data, self.d, self.w, self.eta, self.o.rank_cap, self.o.kick,
                              self.o.max_sweeps, self.rnd)
         self.w = warm
         comps = [tt.unvec_tt(w.component(b)) for b in range(data.nblk)]
-        if data.nblk == 3:
+        if data.masks is not None:
+            dX, dL, dZ = comps
+            pY, pT = data.masks
+            dY = tt.unvec_tt(tt.hadamard(tt.vec_tt(dL), pY))
+            dT = tt.unvec_tt(tt.hadamard(tt.vec_tt(dL), pT))
+        elif data.nblk == 3:
             dX, dY, dZ = comps
             dT = None
         else:
@@ -758,6 +829,8 @@ class TTIPM:
         return min_gen_eig(M, dM, e0, self.rnd, rank, sweeps)
 
     def _max_step(self, M, dM, e0):
+        if self.nu > 0.0:
+            M = tt.add(M, self.I, 1.0, self.nu)
         lam, e = self._gen_eig(M, _sym_tt(dM), e0, self.o.eig_rank, self.o.eig_sweeps)
         return step_from_lambda(lam), e
 
@@ -767,6 +840,8 @@ class TTIPM:
         p = self.p
         idle = tt.add(tt.vec_tt(tt.ones_mat(self.d)), tt.vec_tt(p.ones_t), 1.0, -1.0)
         M = tt.diag_tt(tt.add(v, idle))
+        if self.nu > 0.0:
+            M = tt.add(M, tt.diag_tt(tt.vec_tt(p.ones_t)), 1.0, self.nu)
         lam, e = self._gen_eig(M, tt.diag_tt(dv), e0, 1, self.o.eig_sweeps)
         return step_from_lambda(lam), e
 
@@ -805,8 +880,15 @@ class TTIPM:
         eps_c = o.eps_gap / math.sqrt(self.d)
         info = IterInfo(it, mu, rel_p, rel_d, rel_gap, pobj, dobj)
         self.history.append(info)
-        if rel_p <= eps_p and rel_d <= eps_d and rel_gap <= eps_c:
+        rel_ok = rel_p <= eps_p and rel_d <= eps_d and rel_gap <= eps_c
+        if rel_ok and (o.finish_tol <= 0.0 or self.finish_done):
             return None
+        if rel_ok:
+            merit, done = self.finish_merit()
+            if done:
+                self.finish_done = True
+                return None
+            return self._finish_iteration(it, info, mu, merit)
         self.eta = max(min(self.eta, o.eta_C * mu), o.eta_floor)
         direction = "xz" if it < o.xz_warmup else "aho"
         zero_p = rel_p <= eps_p
@@ -826,6 +908,55 @@ class TTIPM:
         self.prev = dict(X=self.X, Y=self.Y, T=self.T, Z=self.Z, dX=dX, dY=dY, dT=dT, dZ=dZ, ap=ap, ad=ad,
                          tol_p=tol_p, tol_d=tol_d)
         self._apply_update()
+        info.ranks_X = tt.ranks(self.X)
+        info.ranks_Z = tt.ranks(self.Z)
+        info.ranks_W = tt.ranks(self.w.cores)
+        return info
+
+    def finish_merit(self):
+        """Merit of the finishing phase and whether its absolute criteria hold:
+        ||R_p||_F + ||R_d||_F + |<X, Z> + <vec T, s>| and each of the three
+        below finish_tol (Section 3.5)."""
+        rp = tt.norm(self.residual_p())
+        rd = tt.norm(self.residual_d())
+        comp = tt.inner(tt.vec_tt(self.Z), tt.vec_tt(self.X))
+        if self.T is not None:
+            comp += tt.inner(tt.vec_tt(self.T), self.slack(self.X))
+        tol = self.o.finish_tol
+        return rp + rd + abs(comp), (rp < tol and rd < tol and abs(comp) < tol)
+
+    def _finish_iteration(self, it, info, mu, merit):
+        """One iteration of the finishing phase: the Mehrotra direction without
+        zeroed residual blocks, step lengths for the relaxed cone M + nu I >= 0,
+        and the update kept only if the merit decreases while the relative
+        criteria still hold; otherwise the previous iterate is retained and nu
+        grows tenfold, up to nu_max (after which the phase ends)."""
+        o = self.o
+        if self.nu == 0.0:
+            self.nu = o.nu0
+        info.finishing, info.nu, info.merit = True, self.nu, merit
+        self.eta = max(min(self.eta, o.eta_C * mu), o.eta_floor)
+        direction = "xz" if it < o.xz_warmup else "aho"
+        dX, dY, dT, dZ, ap, ad, sweeps, _ = self._mehrotra(direction, mu, False, False)
+        info.alpha_p, info.alpha_d, info.direction, info.sweeps = ap, ad, direction, sweeps
+        saved = (self.X, self.Y, self.T, self.Z)
+        tol_p = self.eta * (1.0 + self.nB) / 10.0
+        tol_d = self.eta * (1.0 + self.nC) / 10.0
+        self.prev = dict(X=self.X, Y=self.Y, T=self.T, Z=self.Z, dX=dX, dY=dY, dT=dT, dZ=dZ, ap=ap, ad=ad,
+                         tol_p=tol_p, tol_d=tol_d)
+        self._apply_update()
+        rel_p, rel_d, rel_gap, _, _ = self.measures()
+        eps = 2.0 * o.eps_gap
+        new_merit, _ = self.finish_merit()
+        if rel_p <= eps and rel_d <= eps and rel_gap <= o.eps_gap / math.sqrt(self.d) and new_merit < merit:
+            info.accepted = True
+        else:
+            info.accepted = False
+            self.X, self.Y, self.T, self.Z = saved
+            self.prev = None
+            if self.nu >= o.nu_max:
+                self.finish_done = True
+            self.nu = min(10.0 * self.nu, o.nu_max)
         info.ranks_X = tt.ranks(self.X)
         info.ranks_Z = tt.ranks(self.Z)
         info.ranks_W = tt.ranks(self.w.cores)

@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
                 ("precision", c_int32), ("max_iters", c_int32), ("max_sweeps", c_int32), ("kick", c_int32),
                 ("eig_rank", c_int32), ("eig_sweeps", c_int32), ("seed", ctypes.c_uint64),
                 ("local_dense_max", c_int32), ("gmres_restart", c_int32), ("gmres_max_iters", c_int32),
-                ("eig_two_site", c_int32), ("time_limit", c_double)]
+                ("eig_two_site", c_int32), ("time_limit", c_double), ("combined_multipliers", c_int32),
+                ("finish_tol", c_double), ("nu0", c_double), ("nu_max", c_double)]
 
 
 class IterInfo(ctypes.Structure):
@@ -46,7 +47,8 @@ class IterInfo(ctypes.Structure):
                 ("max_rank_W", c_int32), ("sweeps", c_int32), ("direction", c_int32), ("seconds", c_double),
                 ("gmres_iters", ctypes.c_int64), ("pred_used", ctypes.c_int64), ("pred_fallbacks", ctypes.c_int64),
                 ("forcing", c_double), ("forcing_corrections", ctypes.c_int64), ("damped_retries", ctypes.c_int64),
-                ("xz_fallbacks", ctypes.c_int64)]
+                ("xz_fallbacks", ctypes.c_int64), ("finishing", c_int32), ("accepted", c_int32), ("nu", c_double),
+                ("merit", c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)

@@ -109,6 +109,14 @@ Options to_options(const tt_sdp_options* o) {
   r.gmres_max_iters = o->gmres_max_iters;
   r.eig_two_site = o->eig_two_site;
   r.time_limit = o->time_limit;
+  r.combined_multipliers = o->combined_multipliers;
+  r.finish_tol = o->finish_tol;
+  r.nu0 = o->nu0;
+  r.nu_max = o->nu_max;
+  TT_CHECK(r.finish_tol >= 0.0 && r.nu0 > 0.0 && r.nu_max >= r.nu0, TT_E_INVALID_ARG,
+           "finishing phase: finish_tol >= 0 and 0 < nu0 <= nu_max");
+  TT_CHECK(r.combined_multipliers == 0 || r.combined_multipliers == 1, TT_E_INVALID_ARG,
+           "combined_multipliers must be 0 or 1");
   TT_CHECK(r.time_limit >= 0.0, TT_E_INVALID_ARG, "time_limit must be >= 0");
   TT_CHECK(r.eig_two_site == 0 || r.eig_two_site == 1, TT_E_INVALID_ARG, "eig_two_site must be 0 or 1");
   TT_CHECK(r.local_dense_max >= 0 && r.gmres_restart > 0 && r.gmres_max_iters > 0, TT_E_INVALID_ARG,
@@ -375,6 +383,10 @@ void tt_sdp_default_options(tt_sdp_options* o) {
   o->gmres_max_iters = 400;
   o->eig_two_site = 1;
   o->time_limit = 0.0;
+  o->combined_multipliers = 1;
+  o->finish_tol = 0.0;
+  o->nu0 = 1e-6;
+  o->nu_max = 1e-3;
 }
 
 }  // extern "C"
@@ -531,6 +543,10 @@ tt_status tt_sdp_newton_step(tt_sdp_ctx* ctx, tt_sdp_iter_info* info) {
     info->forcing_corrections = l.forcing_corrections;
     info->damped_retries = l.retries;
     info->xz_fallbacks = l.fallbacks;
+    info->finishing = l.finishing;
+    info->accepted = l.accepted;
+    info->nu = l.nu;
+    info->merit = l.merit;
   });
 }
 

@@ -144,6 +144,39 @@ struct NewtonData {
   int nblk() const { return ineq ? 4 : 3; }
 };
 
+// Combined multiplier storage (Section 3.5, "Combined Multiplier Storage"):
+// with the non-idle masks P_Y = I - K_Y and P_T = I - K_T disjoint, dY and dT
+// are one block dLambda (dY = P_Y dLambda, dT = P_T dLambda). The multiplier
+// rows become P_Y (p-row) + P_T (t-row):
+//   (-P_Y A_eq + sgn P_T T A_ineq) dX + (P_Y K_Y P_Y + P_T (D_ineq + K_T) P_T) dLambda
+//       = -(P_Y R_p + P_T R_t),
+// the multiplier column of the dZ equation A_eq^T P_Y - sgn A_ineq^T P_T. Every
+// operator here is diag_TT of a vector: products are Hadamard products of the
+// diagonals, and P D P = P D for 0/1 masks. The system then has the block
+// structure of the problem without inequalities (dX, dLambda, dZ).
+struct MaskDiagonals {
+  const DTT &pY, &pT, &aeq, &ain, &ky;
+};
+
+void combine_multipliers(NewtonData& nd, const MaskDiagonals& m) {
+  const double sg = nd.sgn;
+  DTT row = tt_add(tt_hadamard(m.pY, m.aeq), tt_hadamard(m.pT, tt_op_diag(nd.TA)), 1.0, -sg);
+  DTT dk = tt_op_diag(nd.DK[0]);
+  for (size_t i = 1; i < nd.DK.size(); ++i) dk = tt_add(dk, tt_op_diag(nd.DK[i]), 1.0, 1.0);
+  DTT lam = tt_add(tt_hadamard(m.pY, m.ky), tt_hadamard(m.pT, dk), 1.0, 1.0);
+  DTT col = tt_add(tt_hadamard(m.pY, m.aeq), tt_hadamard(m.pT, m.ain), 1.0, -sg);
+  std::vector<RhsTerm> rhs;
+  for (const RhsTerm& t : nd.rp) rhs.push_back({t.coef, tt_diag(tt_hadamard(m.pY, tt_op_diag(t.op))), t.vec});
+  for (const RhsTerm& t : nd.rt) rhs.push_back({t.coef, tt_diag(tt_hadamard(m.pT, tt_op_diag(t.op))), t.vec});
+  nd.A = tt_diag(row);
+  nd.AT = tt_diag(col);
+  nd.K = tt_diag(lam);
+  nd.rp = std::move(rhs);
+  nd.rt.clear();
+  nd.DK.clear();
+  nd.ineq = false;
+}
+
 DTT op_kron_left(const DTT& m) { return tt_kron(m, tt_identity(m.d, 2)); }   // M kron I: vec(M X)
 DTT op_kron_right(const DTT& m) { return tt_kron(tt_identity(m.d, 2), m); }  // I kron M: vec(X M^T)
 DTT vecv(const DTT& m) { return m.view(m.m * m.n, 1); }
@@ -1229,6 +1262,19 @@ Solver::Solver(Problem p, const Options& o) : p_(std::move(p)), o_(o) {
   eta_ = o.eta0;
   nB_ = tt_norm(p_.B_eq);
   nC_ = tt_norm(vecv(p_.C));
+  if (p_.ineq && o.combined_multipliers && tt_is_diag_op(p_.A_eq) && tt_is_diag_op(p_.A_ineq) &&
+      tt_is_diag_op(p_.K_y) && tt_is_diag_op(p_.K_t)) {
+    DTT one = tt_op_diag(tt_identity(d, 4));
+    ky_d_ = tt_op_diag(p_.K_y);
+    kt_d_ = tt_op_diag(p_.K_t);
+    pY_ = tt_add(one, ky_d_, 1.0, -1.0);
+    pT_ = tt_add(one, kt_d_, 1.0, -1.0);
+    if (std::fabs(tt_inner(pY_, pT_)) <= 1e-9) {
+      combined_ = true;
+      aeq_d_ = tt_op_diag(p_.A_eq);
+      ain_d_ = tt_op_diag(p_.A_ineq);
+    }
+  }
 }
 
 DTT Solver::slack(const DTT& X) {
@@ -1246,8 +1292,11 @@ Solver::Measures Solver::measures() {
   m.pobj = tt_inner(vecv(p_.C), vecv(X_));
   m.dobj = tt_inner(p_.B_eq, vecv(Y_));
   if (p_.ineq) m.dobj -= p_.sgn * tt_inner(p_.B_ineq, vecv(T_));
-  m.rel_p = tt_norm(rp) / (1.0 + nB_);
-  m.rel_d = tt_norm(rd) / (1.0 + nC_);
+  m.abs_p = tt_norm(rp);
+  m.abs_d = tt_norm(rd);
+  m.comp = comp;
+  m.rel_p = m.abs_p / (1.0 + nB_);
+  m.rel_d = m.abs_d / (1.0 + nC_);
   m.rel_gap = comp / ((N_ + p_.q) * (1.0 + std::fabs(m.pobj)));
   m.mu = comp / (N_ + p_.q);
   return m;
@@ -1297,6 +1346,7 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
     nd.sgn = p_.sgn;
     nd.rt = {{1.0, tt_diag(vT), s}, {-sigma_mu, idop, vecv(p_.ones_t)}};
     if (ct) nd.rt.push_back({1.0, tt_diag(vecv(*ct)), *cs});
+    if (combined_) combine_multipliers(nd, MaskDiagonals{pY_, pT_, aeq_d_, ain_d_, ky_d_});
   }
   AmenInfo info;
   BlockTT warm;
@@ -1310,11 +1360,17 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
   *sweeps = info.sweeps;
   amen_ok_ = info.converged;
   dX = unvec(w.component(0));
-  dY = unvec(w.component(1));
-  if (p_.ineq) {
+  if (combined_) {
+    const DTT dL = w.component(1);
+    dY = unvec(tt_hadamard(dL, pY_));
+    dT = unvec(tt_hadamard(dL, pT_));
+    dZ = unvec(w.component(2));
+  } else if (p_.ineq) {
+    dY = unvec(w.component(1));
     dT = unvec(w.component(2));
     dZ = unvec(w.component(3));
   } else {
+    dY = unvec(w.component(1));
     dZ = unvec(w.component(2));
   }
   if (dir == 0) {
@@ -1325,8 +1381,10 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
   }
 }
 
-double Solver::max_step(const DTT& M, const DTT& dM, DTT* e) {
+double Solver::max_step(const DTT& M0, const DTT& dM, DTT* e) {
   bool warm = (e == &eX_) ? haveX_ : haveZ_;
+  // finishing phase: the relaxed cone M + nu I >= 0 (Section 3.5)
+  const DTT M = nu_ > 0.0 ? tt_add(M0, I_, 1.0, nu_) : M0;
   double lam = gen_eig(o_, M, tt_sym(dM), e, warm, rnd_, o_.eig_rank, o_.eig_sweeps);
   if (e == &eX_) haveX_ = true; else haveZ_ = true;
   return step_from_lambda(lam);
@@ -1335,6 +1393,7 @@ double Solver::max_step(const DTT& M, const DTT& dM, DTT* e) {
 double Solver::max_step_diag(const DTT& v, const DTT& dv, DTT* e) {
   DTT idle = tt_add(vecv(tt_ones_mat(p_.d, 2)), vecv(p_.ones_t), 1.0, -1.0);
   DTT M = tt_diag(tt_add(v, idle, 1.0, 1.0));
+  if (nu_ > 0.0) M = tt_add(M, tt_diag(vecv(p_.ones_t)), 1.0, nu_);
   bool warm = (e == &eS_) ? haveS_ : haveT_;
   double lam = gen_eig(o_, M, tt_diag(dv), e, warm, rnd_, 1, o_.eig_sweeps);
   if (e == &eS_) haveS_ = true; else haveT_ = true;
@@ -1483,6 +1542,63 @@ struct EventPair {
 };
 }  // namespace
 
+// The finishing phase of Section 3.5 ("Relaxing the Positive Definiteness
+// Barrier"): once the relative criteria hold and an absolute tolerance is
+// set, iterations take the Mehrotra direction without zeroed residual blocks
+// and step lengths for the relaxed cone M + nu I >= 0; an update is kept only
+// if it lowers the merit ||R_p||_F + ||R_d||_F + |<X, Z> + <vec T, s>| while
+// the relative criteria still hold. Otherwise the previous iterate is kept and
+// nu grows tenfold up to nu_max, after which the phase ends.
+void Solver::finish_iteration(IterLog& log, const Measures& ms) {
+  if (nu_ == 0.0) nu_ = o_.nu0;
+  log.finishing = 1;
+  log.nu = nu_;
+  const double merit = ms.abs_p + ms.abs_d + std::fabs(ms.comp);
+  log.merit = merit;
+  eta_ = std::max(std::min(eta_, o_.eta_C * ms.mu), o_.eta_floor);
+  int dir = it_ < o_.xz_warmup ? 0 : 1;
+  DTT dX, dY, dT, dZ;
+  double ap = 0.0, ad = 0.0;
+  int sw = 0;
+  mehrotra(dir, ms.mu, false, false, dX, dY, dT, dZ, &ap, &ad, &sw);
+  log.alpha_p = ap;
+  log.alpha_d = ad;
+  log.direction = dir;
+  log.sweeps = sw;
+  log.max_rank_W = w_->frame.maxrank();
+  const DTT X0 = X_, Y0 = Y_, T0 = T_, Z0 = Z_;
+  last_.X = X_;
+  last_.Y = Y_;
+  last_.T = T_;
+  last_.Z = Z_;
+  last_.dX = dX;
+  last_.dY = dY;
+  last_.dT = dT;
+  last_.dZ = dZ;
+  last_.ap = ap;
+  last_.ad = ad;
+  last_.tol_p = eta_ * (1.0 + nB_) / 10.0;
+  last_.tol_d = eta_ * (1.0 + nC_) / 10.0;
+  last_.valid = true;
+  apply_update();
+  const Measures mn = measures();
+  const double eps = 2.0 * o_.eps_gap, eps_c = o_.eps_gap / std::sqrt((double)p_.d);
+  const double merit_new = mn.abs_p + mn.abs_d + std::fabs(mn.comp);
+  if (mn.rel_p <= eps && mn.rel_d <= eps && mn.rel_gap <= eps_c && merit_new < merit) {
+    log.accepted = 1;
+  } else {
+    log.accepted = 0;
+    X_ = X0;
+    Y_ = Y0;
+    T_ = T0;
+    Z_ = Z0;
+    last_.valid = false;
+    if (nu_ >= o_.nu_max) finish_done_ = true;
+    nu_ = std::min(10.0 * nu_, o_.nu_max);
+  }
+  ++it_;
+}
+
 IterLog Solver::iterate_once() {
   cudaStream_t st = cur_stream();
   EventPair ev;
@@ -1507,8 +1623,15 @@ IterLog Solver::iterate_once() {
   const double eps_c = o_.eps_gap / std::sqrt((double)p_.d);
   TT_CHECK(std::isfinite(ms.mu) && std::isfinite(ms.rel_p) && std::isfinite(ms.rel_d), TT_E_NUMERIC,
            "non-finite residual");
-  if (ms.rel_p <= eps_p && ms.rel_d <= eps_d && ms.rel_gap <= eps_c) {
+  const bool rel_ok = ms.rel_p <= eps_p && ms.rel_d <= eps_d && ms.rel_gap <= eps_c;
+  const double ft = o_.finish_tol;
+  if (rel_ok && ft > 0.0 && !finish_done_ &&
+      (ms.abs_p < ft && ms.abs_d < ft && std::fabs(ms.comp) < ft))
+    finish_done_ = true;  // the absolute criteria of the finishing phase hold
+  if (rel_ok && (ft <= 0.0 || finish_done_)) {
     log.converged = 1;
+  } else if (rel_ok) {
+    finish_iteration(log, ms);
   } else {
     eta_ = std::max(std::min(eta_, o_.eta_C * ms.mu), o_.eta_floor);
     int dir = it_ < o_.xz_warmup ? 0 : 1;

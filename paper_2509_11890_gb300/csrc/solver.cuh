@@ -46,6 +46,9 @@ struct Options {
   double time_limit = 0.0;  // seconds per solve (0: none)
   uint64_t seed = 1234;
   int local_dense_max = 4096, gmres_restart = 40, gmres_max_iters = 400;
+  int combined_multipliers = 1;  // one block dLambda for dY, dT when their masks are disjoint
+  // finishing phase (Section 3.5): absolute tolerance (0: off) and the barrier relaxation range
+  double finish_tol = 0.0, nu0 = 1e-6, nu_max = 1e-3;
 };
 
 struct IterLog {
@@ -59,6 +62,8 @@ struct IterLog {
   long long forcing_corrections = 0;
   long long retries = 0;            // damped retries of updates that left the cone, so far
   long long fallbacks = 0;          // AHO iterations redone with the XZ direction, so far
+  int finishing = 0, accepted = 1;  // finishing-phase iteration; its update was kept
+  double nu = 0.0, merit = 0.0;     // its barrier relaxation; merit of the iterate it started from
 };
 
 class RankPredictor;
@@ -96,6 +101,7 @@ class Solver {
  private:
   struct Measures {
     double rel_p, rel_d, rel_gap, pobj, dobj, mu;
+    double abs_p, abs_d, comp;  // ||R_p||_F, ||R_d||_F, <X, Z> + <vec T, s>
   };
   Measures measures();
   DTT slack(const DTT& X);
@@ -106,6 +112,10 @@ class Solver {
   double max_step_diag(const DTT& v, const DTT& dv, DTT* e);
   DTT round_psd(const DTT& M, double delta, const DTT* shift, int var_id);
   IterLog iterate_once();
+  // one iteration of the finishing phase (Section 3.5); fills log
+  void finish_iteration(IterLog& log, const Measures& ms);
+  double nu_ = 0.0;          // relaxation M + nu I >= 0 of the step lengths
+  bool finish_done_ = false;
   // Mehrotra predictor and corrector solves with their step lengths; returns
   // whether both AMEn solves met their tolerance
   bool mehrotra(int dir, double mu, bool zp, bool zd, DTT& dX, DTT& dY, DTT& dT, DTT& dZ, double* ap, double* ad,
@@ -145,6 +155,11 @@ class Solver {
   DTT eX_, eZ_, eT_, eS_;
   bool haveX_ = false, haveZ_ = false, haveT_ = false, haveS_ = false;
   std::vector<cudaStream_t> side_;  // streams of the concurrent roundings
+  // combined multiplier storage: diagonals of the non-idle masks P_Y, P_T and
+  // of A_eq, A_ineq, K_Y, K_T (set when every one of them is diagonal and the
+  // masks are disjoint)
+  bool combined_ = false;
+  DTT pY_, pT_, aeq_d_, ain_d_, ky_d_, kt_d_;
   bool has_deadline_ = false;
   std::chrono::steady_clock::time_point deadline_;
 };

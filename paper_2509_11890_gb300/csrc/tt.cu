@@ -515,6 +515,35 @@ std::shared_ptr<DBuf<double>> tt_merge_cores(const DTT& op, int k) {
   return out;
 }
 
+namespace {
+// out[p][i][q] = op[p][i][i][q]
+__global__ void op_diag_kernel(const double* __restrict__ op, int R, int m, int R2, double* __restrict__ out) {
+  const long long tot = (long long)R * m * R2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long q = e % R2, i = (e / R2) % m, p = e / ((long long)R2 * m);
+    out[e] = op[((p * m + i) * m + i) * R2 + q];
+  }
+}
+}  // namespace
+
+DTT tt_op_diag(const DTT& op) {
+  TT_CHECK(op.m == op.n, TT_E_SHAPE, "tt_op_diag: square modes expected");
+  DTT t = tt_alloc(op.d, op.r, op.m, 1);
+  for (int k = 0; k < op.d; ++k) {
+    const long long n = t.csize(k);
+    op_diag_kernel<<<grid1(n), 256, 0, cur_stream()>>>(op.core(k), op.r[k], op.m, op.r[k + 1], t.core(k));
+    count_launch();
+  }
+  check_launch("tt_op_diag");
+  return t;
+}
+
+bool tt_is_diag_op(const DTT& op) {
+  if (op.m != op.n) return false;
+  const double all = tt_inner(op, op), dg = tt_norm(tt_op_diag(op));
+  return std::fabs(all - dg * dg) <= 1e-12 * std::max(all, 1e-300);
+}
+
 DTT tt_diag(const DTT& v) {
   int M = v.m * v.n;
   DTT t = tt_alloc(v.d, v.r, M, M);

@@ -52,6 +52,8 @@ DTT tt_kron(const DTT& a, const DTT& b);        // Definition "Kronecker product
 DTT tt_hadamard(const DTT& a, const DTT& b);    // element-wise, ranks multiply
 DTT tt_matvec(const DTT& op, const DTT& v);     // op (m x n) applied to v (mode n)
 DTT tt_diag(const DTT& v);                      // Definition "TT Diagonalisation"
+DTT tt_op_diag(const DTT& op);                  // the diagonal of a square TT matrix, as a TT vector
+bool tt_is_diag_op(const DTT& op);              // all off-diagonal mode entries are zero
 // Operator cores k, k+1 as one core [r_k][(i1 i2)][(j1 j2)][r_{k+2}] (modes m^2 x n^2)
 std::shared_ptr<DBuf<double>> tt_merge_cores(const DTT& op, int k);
 DTT tt_identity(int d, int m);                  // I_m kron ... kron I_m, rank 1

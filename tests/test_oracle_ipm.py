@@ -239,3 +239,73 @@ def test_warm_start_frame_stays_within_the_rank_cap():
         ipm.iterate(it)
         assert ipm.w.pos == 0
         assert max(tt.ranks(ipm.w.cores)) <= cap, tt.ranks(ipm.w.cores)
+
+
+@pytest.mark.parametrize("direction", ["aho", "xz"])
+def test_combined_multiplier_direction_equals_dense_separate_newton(direction):
+    # Section 3.5, "Combined Multiplier Storage": with disjoint masks the
+    # direction found with one block dLambda (dY = P_Y dLambda, dT = P_T dLambda)
+    # is the exact Newton direction of the separate padded system (O3)
+    d = 3
+    inst = inputs.cc_signed(d, 1)
+    prob = tp.corr_clustering(tp.graph_tt(inst["c_plus"]), tp.graph_tt(inst["c_minus"]),
+                              tp.graph_tt(inst["adjacency"]), d)
+    ipm = tt_ipm.TTIPM(prob, tt_ipm.Options(rank_cap=64, kick=4, max_sweeps=8, combined_multipliers=True))
+    _state(ipm, 7)
+    ipm.eta = 1e-12
+    mu = ipm.mu()
+    X, Y, Z, T = (tt.full_mat(m) for m in (ipm.X, ipm.Y, ipm.Z, ipm.T))
+    pad = sd.padded_cc(inst["c_plus"], inst["c_minus"], inst["adjacency"])
+    blocks, K, R = sd.newton_solve(pad, X, Y, Z, T, mu=mu, direction=direction, sigma=0.5)
+    data = ipm.combine_multipliers(ipm.newton_data(direction, 0.5 * mu, None, False, False))
+    assert data.masks is not None and data.nblk == 3
+    dX, dY, dT, dZ, info = ipm.direction(direction, 0.5 * mu, None, False, False)
+    got = [tt.full_mat(m) for m in (dX, dY, dT, dZ)]
+    if direction == "xz":
+        # the XZ direction is symmetrised block by block (reading of Section 3.2)
+        blocks = [0.5 * (b + b.T) for b in blocks]
+    for a, b in zip(got, blocks):
+        np.testing.assert_allclose(a, b, atol=1e-8 * (1 + np.abs(b).max()))
+    # the multipliers live on their own masks
+    n = 2 ** d
+    assert np.abs(got[1][~np.eye(n, dtype=bool)]).max() <= 1e-12 * (1 + np.abs(got[1]).max())
+    assert np.abs(np.diag(got[2])).max() <= 1e-12 * (1 + np.abs(got[2]).max())
+
+
+def test_cc_separate_and_combined_multipliers_reach_the_same_optimum():
+    d = 3
+    inst = inputs.cc_signed(d, 1)
+    prob = tp.corr_clustering(tp.graph_tt(inst["c_plus"]), tp.graph_tt(inst["c_minus"]),
+                              tp.graph_tt(inst["adjacency"]), d)
+    ref = sd.solve_dense(sd.cc_sdp(inst["c_plus"], inst["c_minus"], inst["adjacency"]))
+    for combined in (False, True):
+        ipm = tt_ipm.TTIPM(prob, tt_ipm.Options(rank_cap=16, max_iters=60, combined_multipliers=combined))
+        assert ipm.solve()
+        h = ipm.history[-1]
+        assert abs(h.pobj - ref.pobj) / (1 + abs(ref.pobj)) <= 5e-3, (combined, h)
+
+
+@pytest.mark.parametrize("d,seed", [(5, 1), (6, 0)])
+def test_finishing_phase_reaches_the_absolute_criteria(d, seed):
+    # Section 3.5, "Relaxing the Positive Definiteness Barrier": after the
+    # relative criteria hold, iterations with step lengths for X + nu I >= 0
+    # and merit-controlled acceptance reach ||R_p||, ||R_d||, <X, Z> < 1e-3 and
+    # move the objective closer to the dense optimum
+    inst, prob = _maxcut(d, seed)
+    ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]), tol=1e-10).pobj
+    plain = tt_ipm.TTIPM(prob, tt_ipm.Options(rank_cap=16, max_iters=40))
+    assert plain.solve()
+    fin = tt_ipm.TTIPM(prob, tt_ipm.Options(rank_cap=16, max_iters=40, finish_tol=1e-3))
+    assert fin.solve()
+    merit, done = fin.finish_merit()
+    assert done and merit < 3e-3
+    steps = [h for h in fin.history if h.finishing]
+    assert steps and all(h.nu <= 1e-3 for h in steps)
+    e_plain = abs(plain.history[-1].pobj - ref) / (1 + abs(ref))
+    e_fin = abs(fin.history[-1].pobj - ref) / (1 + abs(ref))
+    assert e_fin <= 0.1 * e_plain, (e_fin, e_plain)
+    # the relaxed barrier allows eigenvalues down to -nu at most
+    assert np.linalg.eigvalsh(tt.full_mat(fin.X))[0] >= -1e-3
+    # the finishing phase never accepts an update that raises the merit
+    merits = [h.merit for h in steps] + [merit]
+    assert all(b <= a for a, b in zip(merits, merits[1:])), merits
