@@ -61,6 +61,9 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="tf32,bf16",
                    help="other precisions solved on the same instance and reported beside the headline form")
+    p.add_argument("--micro", default="", choices=["", "lu"],
+                   help="run a kernel microbenchmark instead of the workload (lu: tt_lu_solve)")
+    p.add_argument("--sizes", default="256,512,1024,2048,4096", help="system sizes of --micro lu")
     p.add_argument("--no-learned", dest="learned", action="store_false",
                    help="skip the FP64 solve with the learned rank predictor")
     p.add_argument("--form-time-limit", type=float, default=60.0,
@@ -708,8 +711,47 @@ def run_batch(a):
     return 0
 
 
+def run_micro_lu(a):
+    """Dense local solve microbenchmark (tt_lu_solve): seeded well-conditioned
+    systems of the sizes the AMEn sweeps form (n x n, n up to 4096), FP64 and
+    FP32-factor / FP64-refined, CUDA events on the launching stream, best of
+    `steps` after `warmup` untimed solves. One JSON line per size and precision."""
+    import torch
+
+    import paper_2509_11890_gb300 as tg
+    from paper_2509_11890_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    for n in [int(x) for x in a.sizes.split(",")]:
+        g = inputs.rng(a.seed, 900 + n)
+        K = torch.from_numpy(g.uniform(-1, 1, (n, n)) + 4.0 * np.eye(n)).cuda()
+        x_true = torch.from_numpy(np.sin(0.37 * np.arange(n) + 1.0)).cuda()
+        b0 = K @ x_true
+        for pn in ("fp64", "tf32"):
+            times, res = [], None
+            for it in range(a.warmup + max(a.steps, 1)):
+                b = b0.clone()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                res = tg.lu_solve(K, b, PREC[pn])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= a.warmup:
+                    times.append(e0.elapsed_time(e1) * 1e-3)
+            err = float(torch.linalg.norm(b - x_true) / torch.linalg.norm(x_true))
+            t = min(times)
+            fl = 2.0 / 3.0 * n ** 3 + 2.0 * n * n
+            print(json.dumps({"micro": "dense local solve (tt_lu_solve)", "n": n, "precision": pn, "seconds": t,
+                              "tflops": fl / t / 1e12, "rel_residual": res, "rel_error": err}), flush=True)
+    return 0
+
+
 def main():
     a = _args()
+    if a.micro == "lu":
+        return run_micro_lu(a)
     if a.impl == "reference":
         return run_reference(a)
     if WORKLOADS[a.workload]["kind"] == "batch":

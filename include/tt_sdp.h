@@ -336,6 +336,17 @@ int32_t tt_sdp_batch_size(const tt_sdp_ctx* ctx);
 /* Instance i of a batch context, owned by the batch (NULL when out of range). */
 tt_sdp_ctx* tt_sdp_batch_member(tt_sdp_ctx* ctx, int32_t i);
 
+/* Row a5, the dense local solve of one AMEn core step (Section 3.3: the
+ * reduced projected system eq. reduced_kkt_system when it is small enough to
+ * be formed): K x = b with K n x n row-major FP64 on the DEVICE (not
+ * modified) and b (n doubles, device) overwritten by x. TT_FP64: LU with
+ * partial pivoting in FP64. Reduced precisions: one FP32 factorisation
+ * refined in FP64 until ||b - K x|| <= 1e-10 ||b|| (at most five
+ * corrections). *rel_residual (host) receives the FP64 relative residual of
+ * the returned x. Synchronises the stream. */
+tt_status tt_lu_solve(int32_t n, const double* K, double* b, int32_t precision, double* rel_residual,
+                      void* stream);
+
 /* Row a9 on host data: TT rounding (Section 2.3, round_TT) followed by the
  * spectral shift of Section 3.4, Corollary psdness_rounding. `in` names HOST
  * cores of a TT matrix (m = n) or vector (n = 1). The input is rounded as a

@@ -548,3 +548,14 @@ def lu_stats():
     f, s, n = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_uint64(0)
     lib().tt_lu_stats(ctypes.byref(f), ctypes.byref(s), ctypes.byref(n))
     return f.value, s.value, n.value
+
+
+def lu_solve(K, b, precision=FP64, stream=None) -> float:
+    """tt_lu_solve: b (device, float64) <- K^{-1} b for a device K (n x n, float64,
+    row-major, kept); returns the FP64 relative residual."""
+    n = int(K.shape[0])
+    assert K.shape == (n, n) and b.numel() == n
+    res = ctypes.c_double(0.0)
+    _check(lib().tt_lu_solve(n, _ptr(K), _ptr(b), int(precision), ctypes.byref(res), _stream(stream)),
+           "tt_lu_solve")
+    return res.value

@@ -93,6 +93,7 @@ SIGNATURES = {
                                       ctypes.POINTER(Allocator), c_void_p, ctypes.POINTER(c_void_p)]),
     "tt_sdp_batch_size": (c_int32, [c_void_p]),
     "tt_sdp_batch_member": (c_void_p, [c_void_p, c_int32]),
+    "tt_lu_solve": (c_int32, [c_int32, c_void_p, c_void_p, c_int32, P_double, c_void_p]),
     "tt_sdp_round": (c_int32, [ctypes.POINTER(TTDesc), c_double, c_int32, c_int32, ctypes.POINTER(TTDesc), P_double,
                                c_void_p]),
     "tt_sdp_create_maxcut": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(Options), c_void_p,

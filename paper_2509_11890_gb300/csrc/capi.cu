@@ -318,6 +318,17 @@ tt_status tt_round(const tt_desc* in, double delta, int32_t rank_cap, int32_t* r
   });
 }
 
+tt_status tt_lu_solve(int32_t n, const double* K, double* b, int32_t precision, double* rel_residual,
+                      void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(n > 0 && K && b && rel_residual, TT_E_INVALID_ARG, "bad tt_lu_solve arguments");
+    TT_CHECK(precision >= TT_FP64 && precision <= TT_MIXED_BF16, TT_E_INVALID_ARG, "unknown precision");
+    int corr = 0;
+    *rel_residual = dense_local_solve(precision, n, const_cast<double*>(K), b, &corr);
+    TT_CUDA(sync_stream(cur_stream()));
+  });
+}
+
 tt_status tt_sdp_round(const tt_desc* in, double tol, int32_t rank_cap, int32_t psd_shift, tt_desc* out,
                        double* zeta_out, void* stream) {
   return guarded(stream, [&] {

@@ -361,14 +361,18 @@ __global__ void __launch_bounds__(kThreads) lu_panel_kernel(int n, T* B, int j0,
 // its jb <= 32 columns) in shared memory for the whole panel, so the column
 // steps touch no global memory: in one CTA when they fit, else split over
 // the CTAs of a thread-block cluster (gridDim.x CTAs, launched as one
-// cluster). Per column: every CTA finds the largest entry among its rows;
-// after a cluster barrier one lane per CTA reads that CTA's candidate
-// through distributed shared memory and the warp picks the pivot (ties to
-// the smaller row, so every CTA picks the same one); the pivot row is read
-// by every CTA and the row it replaces by the pivot's owner; after a second
-// barrier the two rows are exchanged and every CTA scales its rows and
-// applies the rank-1 update. All threads of all CTAs pass the same barriers
-// (no early exit). A one-CTA launch is a cluster of one.
+// cluster). Per column every CTA finds the largest entry among its rows and
+// publishes it together with that row's jb values, and the CTA that holds
+// the diagonal row publishes that row; after one cluster barrier one lane
+// per CTA reads the candidates through distributed shared memory, the warp
+// picks the pivot (ties to the smaller row, so every CTA picks the same one)
+// and reads the winner's published row; the CTAs holding the two rows
+// exchange them in their own tiles, and every CTA scales its rows and
+// applies the rank-1 update. The published buffers alternate between two
+// sets by column parity: a set is rewritten two columns later, after a
+// barrier that every reader of its previous contents has passed. All threads
+// of all CTAs pass the same barriers (no early exit). A one-CTA launch is a
+// cluster of one.
 constexpr int kClusterCtas = 8;
 constexpr int kPanelThreads = 256;
 constexpr int kPanelNB = 32;
@@ -393,10 +397,12 @@ __global__ void __launch_bounds__(kThr)
   };
   extern __shared__ __align__(16) unsigned char panel_smem[];
   T* tile = reinterpret_cast<T*>(panel_smem);  // [chunk][kPanelLds]
-  __shared__ T cand_val;
-  __shared__ int cand_idx;
-  __shared__ T prow[kPanelNB];
-  __shared__ T r0row[kPanelNB];
+  __shared__ T cand_val[2];
+  __shared__ int cand_idx[2];
+  __shared__ T cand_row[2][kPanelNB];   // the candidate's row, published
+  __shared__ T diag_row[2][kPanelNB];   // the diagonal row, published by its holder
+  __shared__ T prow[kPanelNB];          // the pivot row (read)
+  __shared__ T r0row[kPanelNB];         // the diagonal row (read by the pivot's holder)
   __shared__ T red_v[kThr / 32];
   __shared__ int red_i[kThr / 32];
   __shared__ int s_piv;
@@ -411,6 +417,7 @@ __global__ void __launch_bounds__(kThr)
   }
   __syncthreads();
   for (int jj = 0; jj < jb; ++jj) {
+    const int par = jj & 1;
     const int rg = j0 + jj;  // row of the diagonal entry
     T best = T(-1);
     int bi = INT_MAX;
@@ -438,40 +445,44 @@ __global__ void __launch_bounds__(kThr)
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
-      if (lane == 0) { cand_val = best; cand_idx = bi; }
+      if (lane == 0) { cand_val[par] = best; cand_idx[par] = bi; }
+      if (lane < jb) {
+        cand_row[par][lane] = bi != INT_MAX ? tile[(bi - row0) * kPanelLds + lane] : T(0);
+        if (rg >= row0 && rg < row0 + nrows) diag_row[par][lane] = tile[(rg - row0) * kPanelLds + lane];
+      }
     }
-    panel_sync();  // candidates of every CTA are visible
+    panel_sync();  // every CTA's candidate, its row and the diagonal row are visible
     if (warp == 0) {
       T bv = T(-1);
-      int bidx = INT_MAX;
+      int bidx = INT_MAX, bq = 0;
       if (lane < ncta) {
-        bv = *remote(&cand_val, lane);
-        bidx = *remote(&cand_idx, lane);
+        bv = *remote(&cand_val[par], lane);
+        bidx = *remote(&cand_idx[par], lane);
+        bq = lane;
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-        if (oi != INT_MAX && (ov > bv || (ov == bv && oi < bidx) || bidx == INT_MAX)) { bv = ov; bidx = oi; }
+        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+        if (oi != INT_MAX && (ov > bv || (ov == bv && oi < bidx) || bidx == INT_MAX)) { bv = ov; bidx = oi; bq = oq; }
       }
       const int p = bidx;
       const int own_r = (rg - j0) / chunk, own_p = (p - j0) / chunk;
       if (lane < jb) {
-        prow[lane] = remote(tile, own_p)[(p - j0 - own_p * chunk) * kPanelLds + lane];
-        if (crank == own_p && p != rg)
-          r0row[lane] = remote(tile, own_r)[(rg - j0 - own_r * chunk) * kPanelLds + lane];
+        prow[lane] = remote(&cand_row[par][0], bq)[lane];
+        if (crank == own_p && p != rg) r0row[lane] = remote(&diag_row[par][0], own_r)[lane];
       }
       if (lane == 0) {
         s_piv = p;
         if (crank == 0) ipiv[rg] = p;
       }
-    }
-    panel_sync();  // every remote read of this column is done
-    const int p = s_piv;
-    if (warp == 0 && p != rg && lane < jb) {
-      const int own_r = (rg - j0) / chunk, own_p = (p - j0) / chunk;
-      if (crank == own_r) tile[(rg - row0) * kPanelLds + lane] = prow[lane];
-      if (crank == own_p) tile[(p - row0) * kPanelLds + lane] = r0row[lane];
+      __syncwarp();
+      // exchange the two rows in this CTA's own tile
+      if (p != rg && lane < jb) {
+        if (crank == own_r) tile[(rg - row0) * kPanelLds + lane] = prow[lane];
+        if (crank == own_p) tile[(p - row0) * kPanelLds + lane] = r0row[lane];
+      }
     }
     __syncthreads();
     const T pv = prow[jj];
@@ -1092,9 +1103,14 @@ void lu_factor(int n, T* A, int* ipiv, cudaStream_t st) {
   for (int j0 = 0; j0 < n; j0 += nb) {
     int jb = n - j0 < nb ? n - j0 : nb;
     // the active rows in one CTA's shared memory when they fit, else over a
-    // cluster of kClusterCtas CTAs, else the panel streams through L2
+    // cluster of kClusterCtas CTAs, else the panel streams through L2. FP64
+    // panels of more than 256 rows go to the cluster even when they fit one
+    // CTA: their rank-1 updates are FP64 arithmetic, which one SM of GB300
+    // issues at about 8 GFLOP/s, so spreading the rows over eight SMs pays
+    // for the cluster barriers
     const size_t row_bytes = (size_t)kPanelLds * sizeof(T);
-    if ((size_t)(n - j0) * row_bytes <= kPanelSmemMax) {
+    const bool spread = std::is_same<T, double>::value && n - j0 > 256;
+    if (!spread && (size_t)(n - j0) * row_bytes <= kPanelSmemMax) {
       lu_panel_smem_kernel<T, false, 512><<<1, 512, (size_t)(n - j0) * row_bytes, st>>>(n, A, j0, jb, n - j0,
                                                                                        ipiv);
     } else if ((size_t)ceil_div(n - j0, kClusterCtas) * row_bytes <= kPanelSmemMax) {

@@ -828,6 +828,10 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
 
 }  // namespace
 
+double dense_local_solve(int prec, int N, double* K, double* b, int* corrections) {
+  return lu_solve_prec(prec, N, K, b, kLuRefineTol, corrections);
+}
+
 DTT BlockTT::component(int b) const {
   DTT t = frame;
   size_t n0 = frame.csize(pos);

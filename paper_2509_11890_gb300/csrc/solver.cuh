@@ -164,6 +164,12 @@ class Solver {
   std::chrono::steady_clock::time_point deadline_;
 };
 
+// Solves K x = b (N x N row-major FP64 on the device, kept; b becomes x) as the
+// dense local solves of the AMEn sweep do: LU with partial pivoting in FP64, or
+// one FP32 factorisation refined in FP64 for the reduced precisions. Returns
+// the FP64 relative residual; *corrections counts the refinement solves.
+double dense_local_solve(int prec, int N, double* K, double* b, int* corrections);
+
 // min over e of <e, dM e>/<e, M e> (M positive definite): one-site ALS and
 // two-site DMRG sweeps (relative SVD truncation tolerance tol at each split).
 double min_gen_eig(const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank, int sweeps,

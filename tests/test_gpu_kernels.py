@@ -161,3 +161,21 @@ def test_round_cap_and_degenerate():
     g1, z1 = tg.round_tt(tg.DevTT.from_cores(one), 1e-3)
     np.testing.assert_allclose(g1.cores()[0], one[0], atol=1e-15)
     assert z1 == 0.0
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 200, 1100, 2300])
+@pytest.mark.parametrize("prec", [tg.FP64, tg.MIXED_TF32])
+def test_dense_local_solve(n, prec):
+    # tt_lu_solve against numpy's solve of the same system: one panel, ragged
+    # panels, the one-CTA shared-memory panel and (n = 2300 in FP64) the
+    # cluster panel
+    g = inputs.rng(17, n)
+    K = g.standard_normal((n, n)) + 2.0 * np.sqrt(n) * np.eye(n)
+    x = g.standard_normal(n)
+    b = K @ x
+    Kd, bd = _t(K), _t(b)
+    res = tg.lu_solve(Kd, bd, prec)
+    ref = np.linalg.solve(K, b)
+    np.testing.assert_allclose(bd.cpu().numpy(), ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+    assert res <= 1e-10
+    np.testing.assert_array_equal(Kd.cpu().numpy(), K)  # K is not modified
