@@ -61,8 +61,10 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="tf32,bf16",
                    help="other precisions solved on the same instance and reported beside the headline form")
-    p.add_argument("--micro", default="", choices=["", "lu"],
-                   help="run a kernel microbenchmark instead of the workload (lu: tt_lu_solve)")
+    p.add_argument("--micro", default="", choices=["", "lu", "contract"],
+                   help="run a kernel microbenchmark instead of the workload (lu: tt_lu_solve; contract: "
+                        "environment update and local product)")
+    p.add_argument("--shapes", default="16:32,64:128,128:256", help="r:R shapes of --micro contract")
     p.add_argument("--sizes", default="256,512,1024,2048,4096", help="system sizes of --micro lu")
     p.add_argument("--no-learned", dest="learned", action="store_false",
                    help="skip the FP64 solve with the learned rank predictor")
@@ -748,10 +750,61 @@ def run_micro_lu(a):
     return 0
 
 
+def run_micro_contract(a):
+    """Contraction microbenchmark: one left environment update and one local
+    product (three-stage contractions, rows a6 and a7) at the shapes of the
+    configured workloads: frame and vector ranks r, operator ranks R, modes
+    4 x 4, with (r, R) = (16, 32), (64, 128), (128, 256). CUDA events on the
+    launching stream around `steps` calls after `warmup`; algorithmic flops
+    of the three stages (the library's own count)."""
+    import torch
+
+    import paper_2509_11890_gb300 as tg
+    from paper_2509_11890_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peaks, kind = _peaks()
+    for r, R in [(int(x.split(":")[0]), int(x.split(":")[1])) for x in a.shapes.split(",")]:
+        dims = dict(rw=r, rw2=r, R=R, R2=R, rv=r, rv2=r, m=4, n=4)
+        g = inputs.rng(a.seed, 700 + r)
+        t = lambda *sh: torch.from_numpy(g.standard_normal(sh)).cuda()
+        phi, u, op, v, psi = t(r, R, r), t(r, 4, r), t(R, 4, 4, R), t(r, 4, r), t(r, R, r)
+        out = torch.empty(r * R * r, dtype=torch.float64, device="cuda")
+        y = torch.empty(r * 4 * r, dtype=torch.float64, device="cuda")
+        flops = (2.0 * r * R * r * 4 * r + 2.0 * r * r * (R * 4) * (4 * R) + 2.0 * r * R * r * r * 4)
+        for pn in ("fp64", "fp32", "tf32", "bf16"):
+            for name, fn in (("env_left", lambda: tg.env_left_step(dims, phi, u, op, v, out, PREC[pn])),
+                             ("local_apply", lambda: tg.local_apply(dims, phi, op, psi, v, y, PREC[pn]))):
+                for _ in range(a.warmup):
+                    fn()
+                tg.contraction_stats_reset()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(max(a.steps, 1)):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) * 1e-3 / max(a.steps, 1)
+                tf, ts, tl = tg.tc_stats()
+                rec = {"micro": f"{name} (three-stage contraction)", "r": r, "R": R, "precision": pn,
+                       "seconds": sec, "gflop": flops / 1e9, "tflops": flops / sec / 1e12}
+                if tl:
+                    tc = tf / ts / 1e12
+                    pk = peaks["bf16_tflops_sustained"] * (0.5 if pn == "tf32" else 1.0)
+                    rec["tc_gemm"] = {"launches_per_call": tl / max(a.steps, 1), "tflops": tc,
+                                      "frac_of_peak": tc / pk, "peak": pk, "peak_source": f"{kind} bf16 sustained"}
+                print(json.dumps(rec), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.micro == "lu":
         return run_micro_lu(a)
+    if a.micro == "contract":
+        return run_micro_contract(a)
     if a.impl == "reference":
         return run_reference(a)
     if WORKLOADS[a.workload]["kind"] == "batch":

@@ -108,9 +108,10 @@ tt_status tt_local_apply(const tt_contract_dims* dims, const double* phi, const 
  * file-scope device array of 4,194,304 doubles (32 MiB) that every GPU loading
  * the library holds until the process exits. Shapes whose intermediates
  * (rw*R*n*rv2 + rw*m*R2*rv2 doubles) exceed it are rejected with TT_E_NOMEM
- * before anything runs. The first call on a device looks up the array's device
- * address with that device current; make that first call before any stream
- * capture. All calls share the array and it keeps the last call's contents
+ * before anything runs. Every call looks up the array's device address with
+ * the calling thread's current device (so a reset device is handled); make
+ * the first call on a device before any stream capture, since it loads the
+ * module there. All calls share the array and it keeps the last call's contents
  * (every element a call reads it has written itself first, so nothing needs
  * clearing); calls that overlap on the GPU, on different streams or devices
  * sharing a context, race on it. Arguments as for tt_env_left_step. */

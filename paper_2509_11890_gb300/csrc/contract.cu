@@ -533,23 +533,15 @@ namespace {
 constexpr size_t kNoAllocScratch = size_t(1) << 22;  // doubles (32 MiB)
 __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
 
-// Host code cannot use g_noalloc_scratch's name as a device address; the
-// address is looked up once per device, with that device current.
+// Host code cannot use g_noalloc_scratch's name as a device address: the
+// address is looked up with the calling thread's current device, on every
+// call (cheap once the module is loaded), so a context that was reset and
+// recreated never sees a stale address.
 double* noalloc_scratch_ptr() {
-  static std::mutex mu;
-  static double* ptrs[64] = {nullptr};
-  int dev = 0;
-  TT_CUDA(cudaGetDevice(&dev));
-  TT_CHECK(dev >= 0 && dev < 64, TT_E_CUDA, "device index out of range");
-  std::lock_guard<std::mutex> lk(mu);
-  if (!ptrs[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess)
-      throw TTError(TT_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    ptrs[dev] = static_cast<double*>(p);
-  }
-  return ptrs[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) throw TTError(TT_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  return static_cast<double*>(p);
 }
 
 }  // namespace

@@ -4,6 +4,8 @@
 // a 4 x 4 register tile each. The offsets of the tile's rows, columns and
 // of each 16-wide K slice are decomposed once into shared memory, so loading
 // an element is one add; out-of-range rows / columns / k read zero.
+#include <algorithm>
+
 #include "gemm.cuh"
 
 namespace ttsdp {
@@ -39,10 +41,15 @@ __device__ __forceinline__ void offsets_of(int l, const Idx32& idx, int& o0, int
   }
 }
 
+// With ksplit > 1, blockIdx.z = batch * ksplit + split: the CTA sums the K range
+// [split * kchunk, min(Kt, (split + 1) * kchunk)) and writes its partial tile,
+// unscaled, to the dense workspace W[batch][split][m][n] (C is not touched);
+// `split_reduce_kernel` then adds the partials in split order into C.
 template <typename T>
 __global__ void __launch_bounds__(NT) gemm_nd_kernel(Gemm32 g, const T* __restrict__ A,
                                                      const T* __restrict__ B, T* __restrict__ C,
-                                                     T alpha, T beta, int Mt, int Nt, int Kt) {
+                                                     T alpha, T beta, int Mt, int Nt, int Kfull, int ksplit,
+                                                     int kchunk, T* __restrict__ W) {
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   __shared__ int offAM[BM], offCM[BM], offBN[BN], offCN[BN];
@@ -52,9 +59,13 @@ __global__ void __launch_bounds__(NT) gemm_nd_kernel(Gemm32 g, const T* __restri
   const int n0 = blockIdx.x * BN;
   const int tid = threadIdx.x;
 
+  const int split = ksplit > 1 ? (int)(blockIdx.z % ksplit) : 0;
+  const int bz = ksplit > 1 ? (int)(blockIdx.z / ksplit) : (int)blockIdx.z;
+  const int kbeg = split * kchunk;
+  const int Kt = ksplit > 1 ? min(Kfull - kbeg, kchunk) : Kfull;  // this CTA's K length
   int baseA = 0, baseB = 0, baseC = 0;
   {
-    int l = blockIdx.z;
+    int l = bz;
 #pragma unroll
     for (int i = kMaxSub - 1; i >= 0; --i) {
       if (i < g.B.nsub) {
@@ -85,7 +96,7 @@ __global__ void __launch_bounds__(NT) gemm_nd_kernel(Gemm32 g, const T* __restri
   if (ktab) {
     for (int k = tid; k < Kt; k += NT) {
       int oa, ob;
-      offsets_of(k, g.K, oa, ob);
+      offsets_of(kbeg + k, g.K, oa, ob);
       offAK[k] = oa;
       offBK[k] = ob;
     }
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(NT) gemm_nd_kernel(Gemm32 g, const T* __restri
     if (!ktab && tid < BK) {
       const int k = k0 + tid;
       int oa = -1, ob = -1;
-      if (k < Kt) offsets_of(k, g.K, oa, ob);
+      if (k < Kt) offsets_of(kbeg + k, g.K, oa, ob);
       offAK[tid] = oa;
       offBK[tid] = ob;
     }
@@ -140,6 +151,20 @@ __global__ void __launch_bounds__(NT) gemm_nd_kernel(Gemm32 g, const T* __restri
     }
   }
   __syncthreads();
+  if (ksplit > 1) {
+    T* w = W + ((long long)bz * ksplit + split) * (long long)Mt * Nt;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + ty + 16 * i;
+      if (m >= Mt) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n < Nt) w[(long long)m * Nt + n] = acc[i][j];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int om = offCM[ty + 16 * i];
@@ -153,6 +178,34 @@ __global__ void __launch_bounds__(NT) gemm_nd_kernel(Gemm32 g, const T* __restri
       if (beta != T(0)) v += beta * (*c);
       *c = v;
     }
+  }
+}
+
+// C[batch][m][n] = alpha * sum over the splits of W[batch][split][m][n] + beta * C,
+// the splits added in index order (deterministic)
+template <typename T>
+__global__ void split_reduce_kernel(Gemm32 g, T* __restrict__ C, const T* __restrict__ W, T alpha, T beta,
+                                    int Mt, int Nt, int Bt, int ksplit) {
+  const long long tot = (long long)Bt * Mt * Nt;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(e % Nt), m = (int)((e / Nt) % Mt), bz = (int)(e / ((long long)Nt * Mt));
+    T acc = T(0);
+    for (int s = 0; s < ksplit; ++s) acc += W[(((long long)bz * ksplit + s) * Mt + m) * Nt + n];
+    int baseC = 0, l = bz;
+    for (int i = kMaxSub - 1; i >= 0; --i) {
+      if (i < g.B.nsub) {
+        const int ex = g.B.ext[i];
+        baseC += (l % ex) * g.bC[i];
+        l /= ex;
+      }
+    }
+    int oa, om, ob, on;
+    offsets_of(m, g.M, oa, om);
+    offsets_of(n, g.N, ob, on);
+    T* c = C + baseC + om + on;
+    T v = alpha * acc;
+    if (beta != T(0)) v += beta * (*c);
+    *c = v;
   }
 }
 
@@ -197,10 +250,30 @@ void gemm_nd(const GemmND& g, const T* A, size_t nA, const T* B, size_t nB, T* C
     d.bB[i] = (int)g.bB.s[i];
     d.bC[i] = (int)g.cB.s[i];
   }
-  dim3 grid((unsigned)((Nt + BN - 1) / BN), (unsigned)((Mt + BM - 1) / BM), (unsigned)Bt);
-  gemm_nd_kernel<T><<<grid, NT, 0, st>>>(d, A, B, C, alpha, beta, (int)Mt, (int)Nt, (int)Kt);
+  // few output tiles and a long K: split K over CTAs so that the launch fills
+  // the SMs (at least 256 k per split, at most 64 splits)
+  const long long tiles = ((Nt + BN - 1) / BN) * ((Mt + BM - 1) / BM) * Bt;
+  int ksplit = 1;
+  if (tiles < 152 && Kt >= 512) {
+    ksplit = (int)std::min<long long>(std::min<long long>((2 * 152 + tiles - 1) / tiles, Kt / 256), 64);
+    while (ksplit > 1 && Bt * ksplit > 65535) --ksplit;
+  }
+  const int kchunk = ksplit > 1 ? (int)((Kt + ksplit - 1) / ksplit) : (int)Kt;
+  if (ksplit > 1) ksplit = (int)((Kt + kchunk - 1) / kchunk);
+  DBuf<T> work;
+  if (ksplit > 1) work.alloc((size_t)Bt * ksplit * Mt * Nt);
+  dim3 grid((unsigned)((Nt + BN - 1) / BN), (unsigned)((Mt + BM - 1) / BM), (unsigned)(Bt * ksplit));
+  gemm_nd_kernel<T><<<grid, NT, 0, st>>>(d, A, B, C, alpha, beta, (int)Mt, (int)Nt, (int)Kt, ksplit, kchunk,
+                                         work.get());
   count_launch();
   check_launch("gemm_nd_kernel");
+  if (ksplit > 1) {
+    const long long tot = Bt * Mt * Nt;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 152 * 16);
+    split_reduce_kernel<T><<<blocks, 256, 0, st>>>(d, C, work.get(), alpha, beta, (int)Mt, (int)Nt, (int)Bt, ksplit);
+    count_launch();
+    check_launch("split_reduce_kernel");
+  }
 }
 
 namespace {
