@@ -253,6 +253,8 @@ typedef struct {
                               the iterate and multiplies nu by 10, up to nu_max,
                               after which the phase ends                          */
   double nu0, nu_max;      /* first and largest relaxation nu (1e-6, 1e-3)            */
+  int32_t refine_sweeps;   /* reduced precisions: FP64 sweeps that close every AMEn
+                              solve (1 by default; 1..8)                           */
 } tt_sdp_options;
 
 typedef struct tt_sdp_ctx tt_sdp_ctx;

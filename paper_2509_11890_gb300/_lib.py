@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
                 ("eig_rank", c_int32), ("eig_sweeps", c_int32), ("seed", ctypes.c_uint64),
                 ("local_dense_max", c_int32), ("gmres_restart", c_int32), ("gmres_max_iters", c_int32),
                 ("eig_two_site", c_int32), ("time_limit", c_double), ("combined_multipliers", c_int32),
-                ("finish_tol", c_double), ("nu0", c_double), ("nu_max", c_double)]
+                ("finish_tol", c_double), ("nu0", c_double), ("nu_max", c_double), ("refine_sweeps", c_int32)]
 
 
 class IterInfo(ctypes.Structure):

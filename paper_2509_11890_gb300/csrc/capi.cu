@@ -113,6 +113,8 @@ Options to_options(const tt_sdp_options* o) {
   r.finish_tol = o->finish_tol;
   r.nu0 = o->nu0;
   r.nu_max = o->nu_max;
+  r.refine_sweeps = o->refine_sweeps;
+  TT_CHECK(r.refine_sweeps >= 1 && r.refine_sweeps <= 8, TT_E_INVALID_ARG, "refine_sweeps must be in 1..8");
   TT_CHECK(r.finish_tol >= 0.0 && r.nu0 > 0.0 && r.nu_max >= r.nu0, TT_E_INVALID_ARG,
            "finishing phase: finish_tol >= 0 and 0 < nu0 <= nu_max");
   TT_CHECK(r.combined_multipliers == 0 || r.combined_multipliers == 1, TT_E_INVALID_ARG,
@@ -398,6 +400,7 @@ void tt_sdp_default_options(tt_sdp_options* o) {
   o->finish_tol = 0.0;
   o->nu0 = 1e-6;
   o->nu_max = 1e-3;
+  o->refine_sweeps = 1;
 }
 
 }  // extern "C"

@@ -421,7 +421,8 @@ double sweep_floor(int prec) {
   }
 }
 
-// FP64 sweeps that refine a direction found in a reduced precision
+// FP64 sweeps that refine a direction found in a reduced precision (default;
+// Options::refine_sweeps)
 constexpr int kRefineSweeps = 1;
 
 // Relative truncation tolerance of a block move in a sweep of precision
@@ -437,7 +438,8 @@ double move_tol(double tol, int prec) { return std::max(tol, sweep_floor(prec));
 // as the warm start of the next solve.
 BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap, int kick, int max_sweeps,
                    Counter& rnd, int prec_in, int dense_max, int gmres_restart, int gmres_maxit, AmenInfo* info,
-                   BlockTT* warm, const std::chrono::steady_clock::time_point* deadline) {
+                   BlockTT* warm, const std::chrono::steady_clock::time_point* deadline,
+                   int refine_sweeps = kRefineSweeps) {
   // sweeps run in prec_in until they stall at its floor (or use the sweep
   // budget), then up to kRefineSweeps FP64 sweeps refine the direction with
   // FP64 environments, local operators and solves
@@ -480,7 +482,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
   std::vector<int> blockshape = {frame.r[0], 4, frame.r[1]};
   int sweep = 0;
   double max_change = 0.0;
-  const int budget = max_sweeps + (prec_in != TT_FP64 ? kRefineSweeps : 0);
+  const int budget = max_sweeps + (prec_in != TT_FP64 ? refine_sweeps : 0);
   for (sweep = 0; sweep < budget; ++sweep) {
     const bool forward = sweep % 2 == 0;
     max_change = 0.0;
@@ -768,7 +770,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
       }
     } else {
       ++refine;
-      if (max_change < tol || refine >= kRefineSweeps) {
+      if (max_change < tol || refine >= refine_sweeps) {
         ++sweep;
         break;
       }
@@ -1356,7 +1358,7 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
   BlockTT warm;
   BlockTT w = amen_solve(nd, d, w_ ? w_.get() : nullptr, eta_, o_.rank_cap, o_.kick, o_.max_sweeps, rnd_,
                          o_.prec, o_.local_dense_max, o_.gmres_restart, o_.gmres_max_iters, &info, &warm,
-                         has_deadline_ ? &deadline_ : nullptr);
+                         has_deadline_ ? &deadline_ : nullptr, o_.refine_sweeps);
   gmres_iters_ += info.gmres_iters;
   forcing_it_ = std::max(forcing_it_, info.forcing);
   corrections_ += info.corrections;

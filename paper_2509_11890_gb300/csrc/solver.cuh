@@ -49,6 +49,7 @@ struct Options {
   int combined_multipliers = 1;  // one block dLambda for dY, dT when their masks are disjoint
   // finishing phase (Section 3.5): absolute tolerance (0: off) and the barrier relaxation range
   double finish_tol = 0.0, nu0 = 1e-6, nu_max = 1e-3;
+  int refine_sweeps = 1;  // closing FP64 sweeps of a reduced-precision AMEn solve
 };
 
 struct IterLog {
