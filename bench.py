@@ -42,6 +42,11 @@ WORKLOADS = {
     "maxcut_d10_kron_cap64": dict(kind="maxcut", d=10, cap=64),
     "maxcut_d10_kron_er_cap64": dict(kind="maxcut_er", d=10, cap=64),
     "maxcut_d6_kron_cap16": dict(kind="maxcut", d=6, cap=16),
+    # Lovasz theta, n = 2^10: hypercube Q_10 OR Kronecker extras (density ~1%), cap 64
+    "theta_d10_hypercube_cap64": dict(kind="theta", d=10, cap=64, sub_d=6),
+    # correlation clustering, n = 2^12, complete signed graph, cap 128; the oracle checks the
+    # principal 2^6 sub-instance
+    "cc_d12_signed_cap128": dict(kind="cc", d=12, cap=128, sub_d=6),
     # 64 independent Kronecker Max-Cut instances, d ~ U{6..11}, unit weights
     "maxcut_batch64_d6to11_cap64": dict(kind="batch", count=64, d_lo=6, d_hi=11, cap=64, d=11),
 }
@@ -202,8 +207,15 @@ def run_reference(a):
     w = WORKLOADS[a.workload]
     if w["kind"] == "batch":
         return _run_reference_batch(a, w)
-    inst = _instance(w, a.seed)
-    p = sd.maxcut_sdp(inst["weights"])
+    sample = "the same instance"
+    if w["kind"] in ("theta", "cc"):
+        # the dense IPM cannot take these sizes: the oracle runs on the 2^sub_d instance
+        inst = _other_instance(w["kind"], w["sub_d"], a.seed, full_d=w["d"] if w["kind"] == "cc" else None)
+        p = _dense_sdp(w["kind"], inst)
+        sample = f"the 2^{w['sub_d']} instance of the family (the full size is beyond the dense IPM)"
+    else:
+        inst = _instance(w, a.seed)
+        p = sd.maxcut_sdp(inst["weights"])
     times = []
     res = None
     for _ in range(max(a.steps, 1)):
@@ -218,7 +230,7 @@ def run_reference(a):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": a.workload, "n": 2 ** w["d"], "d": w["d"], "seed": a.seed},
         "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle",
-                         "sample": "dense HKM primal-dual IPM (oracle O2) on the same instance to relative gap 1e-4, "
+                         "sample": f"dense HKM primal-dual IPM (oracle O2) on {sample} to relative gap 1e-4, "
                                    f"{res.iters} iterations, median of {len(times)} solves"},
         "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "oracle_pobj": res.pobj,
@@ -593,6 +605,125 @@ def run_ours(a):
     return 0
 
 
+def _other_context(tg, torch, kind, inst, opts):
+    """theta / correlation-clustering context from dense host graphs, converted
+    to TT on the device (row a1)."""
+    tt = lambda m: tg.tt_from_dense(torch.from_numpy(np.ascontiguousarray(m, dtype=np.float64)).cuda(),
+                                    eps_rel=1e-13)
+    if kind == "theta":
+        return tg.Context.theta(tt(inst["adjacency"]), opts)
+    return tg.Context.cc(tt(inst["c_plus"]), tt(inst["c_minus"]), tt(inst["adjacency"]), opts)
+
+
+def _other_instance(kind, d, seed, full_d=None):
+    from paper_2509_11890_gb300 import inputs
+    if kind == "theta":
+        return inputs.theta_hypercube_kron(d, seed)
+    if full_d is not None and full_d != d:
+        return inputs.cc_signed_sub(full_d, d, seed)
+    return inputs.cc_signed(d, seed)
+
+
+def _dense_sdp(kind, inst):
+    from oracle import sdp_dense as sd
+    if kind == "theta":
+        return sd.theta_sdp(inst["adjacency"])
+    return sd.cc_sdp(inst["c_plus"], inst["c_minus"], inst["adjacency"])
+
+
+def _iterate_bounded(tg, ctx, steps, limit):
+    """Up to `steps` iterations, stopping at the first certified one, at a
+    solver error (its status is recorded) or once `limit` wall seconds pass."""
+    infos, err = [], None
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        try:
+            info = ctx.newton_step()
+        except tg.TTSDPError as e:
+            err = {"status": e.status, "message": str(e)}
+            break
+        infos.append(info)
+        if info["converged"] or time.perf_counter() - t0 > limit:
+            break
+    return infos, err, time.perf_counter() - t0
+
+
+def run_other(a):
+    """Lovasz theta (n = 2^10) and correlation clustering (n = 2^12): the plain
+    FP64 solve with the timed steps bounded by a wall-clock limit; value is the
+    time-to-gap, or null with the reason (a solver status or the limit). The
+    oracle's dense IPM checks the same method on a 2^sub_d instance of the
+    family (for correlation clustering the principal sub-instance of the same
+    graph), which is also the CPU baseline."""
+    import torch
+
+    import paper_2509_11890_gb300 as tg
+
+    torch.cuda.set_device(0)
+    w = WORKLOADS[a.workload]
+    kind = w["kind"]
+    inst = _other_instance(kind, w["d"], a.seed)
+    opts = tg.default_options(rank_cap=w["cap"], precision=PREC[a.precision], max_iters=a.steps + 2)
+    stream = torch.cuda.current_stream()
+    ctx = _other_context(tg, torch, kind, inst, opts)
+    torch.cuda.synchronize()
+    tg.contraction_stats_reset()
+    l0 = tg.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        ev0.record(stream)
+        infos, err, wall = _iterate_bounded(tg, ctx, a.steps, a.time_limit)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ctx.close()
+    total = ev0.elapsed_time(ev1) * 1e-3
+    conv = [i for i in infos if i["converged"]]
+    ttg = sum(i["seconds"] for i in infos) if conv else None
+    last = infos[-1] if infos else None
+    lflops, lsec, lcalls = tg.lu_stats()
+    cflops, csec = tg.contraction_stats()
+    # the same method against the dense oracle on the small instance
+    sub = _other_instance(kind, w["sub_d"], a.seed, full_d=w["d"] if kind == "cc" else None)
+    sctx = _other_context(tg, torch, kind, sub, tg.default_options(rank_cap=w["cap"], max_iters=60,
+                                                                     time_limit=a.time_limit))
+    sinfos, serr, _ = _iterate_bounded(tg, sctx, 60, a.time_limit)
+    sctx.close()
+    from oracle import sdp_dense as sd
+    t0 = time.perf_counter()
+    ref = sd.solve_dense(_dense_sdp(kind, sub), tol=1e-8)
+    t_ref = time.perf_counter() - t0
+    s_last = sinfos[-1] if sinfos else None
+    line = {
+        "metric": "time-to-gap-1e-4 (s)", "value": ttg, "unit": "s", "n_gpus": 1, "steps": a.steps,
+        "warmup": 0, "ms_per_step": total / max(len(infos), 1) * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[a.precision], "data": "synthetic",
+        "config": {"workload": a.workload, "n": 2 ** w["d"], "d": w["d"], "rank_cap": w["cap"], "seed": a.seed,
+                   "parallelism": "single", "l2": "no flush"},
+        "gap_reached": bool(conv), "iterations_run": len(infos), "wall_s": wall,
+        "final": ({k: last[k] for k in ("iter", "rel_gap", "rel_p", "rel_d", "pobj", "dobj", "max_rank_X",
+                                        "max_rank_Z", "max_rank_W", "gmres_iters", "xz_fallbacks",
+                                        "damped_retries")} if last else None),
+        "iter_ms": [round(i["seconds"] * 1e3, 1) for i in infos],
+        "lu_share": lsec / total if total > 0 else None, "contraction_share": csec / total if total > 0 else None,
+        "gpu_launches": tg.launch_count() - l0, "clocks": clk.summary(),
+        "sub_instance": {"d": w["sub_d"], "p_star": ref.pobj,
+                         "gpu_pobj": s_last["pobj"] if s_last else None,
+                         "gap_reached": bool(s_last and s_last["converged"]),
+                         "err_vs_oracle_p_star": (abs(s_last["pobj"] - ref.pobj) / (1 + abs(ref.pobj))
+                                                  if s_last else None),
+                         "error": serr},
+        "cpu_baseline": {"value": t_ref, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"dense IPM (oracle O2) on the 2^{w['sub_d']} instance "
+                                   f"({'principal sub-instance' if kind == 'cc' else 'same family'}) to 1e-8"},
+        "e2e": None,
+    }
+    if not conv:
+        line["null_reason"] = (f"solver status {err['status']}: {err['message']}" if err else
+                               "the certified gap was not reached within the timed steps or the time limit")
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(a):
     """Batched solve: every step solves all instances of the batch concurrently
     (tt_sdp_solve_batch: worker threads, one CUDA stream each); the value is
@@ -809,6 +940,8 @@ def main():
         return run_reference(a)
     if WORKLOADS[a.workload]["kind"] == "batch":
         return run_batch(a)
+    if WORKLOADS[a.workload]["kind"] in ("theta", "cc"):
+        return run_other(a)
     return run_ours(a)
 
 
