@@ -69,6 +69,13 @@ class Counter:
         self.n += cnt
         return v.reshape(shape)
 
+    def fork(self) -> "Counter":
+        """A counter seeded by the raw 64-bit value of this stream's next draw
+        (one draw consumed): a sub-stream whose length does not move this one."""
+        x = splitmix64((self.seed ^ ((self.n * 0x9E3779B97F4A7C15) & _M64)) & _M64)
+        self.n += 1
+        return Counter(x)
+
 
 # ----------------------------------------------------------------------------
 # operator terms on the vec_TT space (4 x 4 mode cores)
@@ -481,7 +488,7 @@ def dmrg_keep(s: np.ndarray, tol: float, cap: int) -> int:
 
 
 def min_gen_eig_dmrg(M: list, dM: list, e0: list | None, rnd: Counter, rank: int = 4, sweeps: int = 4,
-                     tol: float = 1e-8):
+                     tol: float = 1e-8, stall: float = 0.0):
     """min over TT vectors e of <e, dM e> / <e, M e> by two-site (DMRG) sweeps (Section 3.4).
 
     The unknown at bond (k, k+1) is the supercore of cores k and k+1; its
@@ -511,6 +518,10 @@ def min_gen_eig_dmrg(M: list, dM: list, e0: list | None, rnd: Counter, rank: int
     Dm = [merge_op_cores(dM, k) for k in range(d - 1)]
     lam = math.inf
     for sweep in range(sweeps):
+        # stop once the quotient of a full sweep has stalled (after two sweeps)
+        if sweep >= 2 and stall > 0.0 and abs(lam - lam_prev) <= stall * abs(lam):
+            break
+        lam_prev = lam
         forward = sweep % 2 == 0
         bonds = range(d - 1) if forward else range(d - 2, -1, -1)
         for k in bonds:
@@ -571,6 +582,7 @@ class Options:
     eig_rank: int = 4
     eig_sweeps: int = 4
     eig_two_site: bool = True   # two-site DMRG sweeps (Section 3.4); False: one-site ALS
+    eig_stall: float = 1e-9     # two-site sweeps stop once a sweep changes the quotient by less (relative)
     max_retries: int = 4        # damp-and-retry of an update that left the cone (Section 3.5)
     combined_multipliers: bool = True  # one block dLambda for dY and dT when their masks are disjoint (Section 3.5)
     # finishing phase (Section 3.5, "Relaxing the Positive Definiteness Barrier"): after
@@ -824,9 +836,12 @@ class TTIPM:
         return min(1.0, self.o.damping * a_p), min(1.0, self.o.damping * a_d)
 
     def _gen_eig(self, M, dM, e0, rank, sweeps):
+        # the eigensolver's random starts and kicks come from a sub-stream, so
+        # how many sweeps it runs does not move the main stream
+        sub = self.rnd.fork()
         if self.o.eig_two_site:
-            return min_gen_eig_dmrg(M, dM, e0, self.rnd, rank, sweeps)
-        return min_gen_eig(M, dM, e0, self.rnd, rank, sweeps)
+            return min_gen_eig_dmrg(M, dM, e0, sub, rank, sweeps, stall=self.o.eig_stall)
+        return min_gen_eig(M, dM, e0, sub, rank, sweeps)
 
     def _max_step(self, M, dM, e0):
         if self.nu > 0.0:

@@ -1043,7 +1043,7 @@ static int dmrg_keep(const std::vector<double>& s, double tol, int cap) {
 // to `rank` (kick) and re-orthonormalised by QR, and the other factor is the
 // projection of the supercore onto it.
 double min_gen_eig_dmrg(const DTT& M, const DTT& dM, DTT* e_io, bool warm, Counter& rnd, int rank, int sweeps,
-                        int prec, double tol) {
+                        int prec, double tol, double stall) {
   const int d = M.d, nmode = M.m;
   if (d < 2) return min_gen_eig(M, dM, e_io, warm, rnd, rank, sweeps, prec);
   cudaStream_t st = cur_stream();
@@ -1073,8 +1073,11 @@ double min_gen_eig_dmrg(const DTT& M, const DTT& dM, DTT* e_io, bool warm, Count
     Dm[k] = tt_merge_cores(dM, k);
   }
   const int n2 = nmode * nmode;
-  double lam = std::numeric_limits<double>::infinity();
+  double lam = std::numeric_limits<double>::infinity(), lam_prev = lam;
   for (int sw = 0; sw < sweeps; ++sw) {
+    // stop once the quotient of a full sweep has stalled (after two sweeps)
+    if (sw >= 2 && stall > 0.0 && std::fabs(lam - lam_prev) <= stall * std::fabs(lam)) break;
+    lam_prev = lam;
     const bool forward = sw % 2 == 0;
     for (int step = 0; step + 1 < d; ++step) {
       const int k = forward ? step : d - 2 - step;
@@ -1229,8 +1232,11 @@ Problem build_cc(const DTT& cp, const DTT& cm, const DTT& a) {
 // or one-site ALS, FP64 throughout.
 static double gen_eig(const Options& o, const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank,
                       int sweeps) {
-  if (o.eig_two_site) return min_gen_eig_dmrg(M, dM, e, warm, rnd, rank, sweeps, TT_FP64, kDmrgTol);
-  return min_gen_eig(M, dM, e, warm, rnd, rank, sweeps, TT_FP64);
+  // the eigensolver's random starts and kicks come from a sub-stream, so how
+  // many sweeps it runs does not move the main stream
+  Counter sub = rnd.fork();
+  if (o.eig_two_site) return min_gen_eig_dmrg(M, dM, e, warm, sub, rank, sweeps, TT_FP64, kDmrgTol, kEigStall);
+  return min_gen_eig(M, dM, e, warm, sub, rank, sweeps, TT_FP64);
 }
 
 void Solver::set_deadline(double seconds_from_now) {

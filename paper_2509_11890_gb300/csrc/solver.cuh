@@ -175,8 +175,11 @@ double dense_local_solve(int prec, int N, double* K, double* b, int* corrections
 // two-site DMRG sweeps (relative SVD truncation tolerance tol at each split).
 double min_gen_eig(const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank, int sweeps,
                    int prec);
+// two-site sweeps stop once a full sweep changes the quotient by at most
+// stall times its size (after two sweeps; 0: run every sweep)
 double min_gen_eig_dmrg(const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank, int sweeps,
-                        int prec, double tol);
+                        int prec, double tol, double stall = 0.0);
 constexpr double kDmrgTol = 1e-8;
+constexpr double kEigStall = 1e-9;
 
 }  // namespace ttsdp

@@ -869,6 +869,14 @@ static inline uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+Counter Counter::fork() {
+  Counter c;
+  c.seed = splitmix64(seed ^ (n * 0x9E3779B97F4A7C15ULL));
+  c.n = 0;
+  ++n;
+  return c;
+}
+
 std::vector<double> Counter::draw(size_t count) {
   std::vector<double> out(count);
   for (size_t j = 0; j < count; ++j) {

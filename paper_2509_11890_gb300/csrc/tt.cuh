@@ -102,6 +102,9 @@ int truncation_rank(const std::vector<double>& s, double thr, int cap);
 struct Counter {
   uint64_t seed = 0, n = 0;
   std::vector<double> draw(size_t count);
+  // a counter seeded by the raw 64-bit value of this stream's next draw (one
+  // draw consumed): a sub-stream whose length does not move this one
+  Counter fork();
 };
 
 // misc device helpers
