@@ -179,3 +179,35 @@ def test_dense_local_solve(n, prec):
     np.testing.assert_allclose(bd.cpu().numpy(), ref, rtol=0, atol=1e-10 * np.abs(ref).max())
     assert res <= 1e-10
     np.testing.assert_array_equal(Kd.cpu().numpy(), K)  # K is not modified
+
+
+def _stress_inputs():
+    # unfoldings with at least 16 columns and twice as many rows, where the
+    # FP64 tall-skinny QR (CholeskyQR2) and the SVD's first-order Jacobi
+    # finish meet their fallback conditions
+    d = 6
+    x = _rtt([4] * d, 20, 50)
+    yield "rank-deficient", tt.add(x, x, 1.0, 0.5), 1e-6          # exact duplicate columns
+    c = [core.copy() for core in x]
+    c[2][:, :, 0] *= 1e-9                                           # an ill-conditioned core
+    yield "ill-conditioned", c, 1e-3
+    rep = [core.copy() for core in x]
+    u, _, vt = np.linalg.svd(rep[3].reshape(-1, rep[3].shape[-1]), full_matrices=False)
+    rep[3] = (u @ vt).reshape(rep[3].shape)                         # all singular values equal
+    yield "repeated singular values", rep, 1e-4
+
+
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_round_fallback_paths_match_oracle(case):
+    name, s, rel = list(_stress_inputs())[case]
+    nrm = tt.norm(s)
+    ref, zeta_ref, ties = tt.round_tt(s, rel * nrm)
+    got, zeta = tg.round_tt(tg.DevTT.from_cores(s), rel * nrm)
+    for k, (rg, rr) in enumerate(zip(got.ranks, tt.ranks(ref))):
+        if 0 < k < len(s) and not ties[k - 1]:
+            assert rg == rr, (name, k, got.ranks, tt.ranks(ref))
+    assert math.isclose(zeta, zeta_ref, rel_tol=1e-6, abs_tol=1e-12 * nrm), (name, zeta, zeta_ref)
+    # the rounded tensor differs from the input by zeta (dense check: a TT
+    # difference norm cannot resolve 1e-10 of the input's norm)
+    err = np.linalg.norm(tt.full_vec(got.cores()) - tt.full_vec(s))
+    assert math.isclose(err, zeta, rel_tol=1e-4, abs_tol=1e-12 * nrm), (name, err, zeta)

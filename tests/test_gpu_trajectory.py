@@ -83,3 +83,44 @@ def test_binding_rank_cap_is_the_method_not_the_gpu():
         # no iterate beats the Eckart-Young bound of the capped rank
         assert info["rel_d"] >= lb["rel_d_lower_bound"] * (1 - 1e-9)
         assert not info["converged"]
+
+
+def test_theta_fp64_solve_follows_oracle_ipm_every_iteration():
+    # Lovasz theta (Section 4.2: A_eq carries the trace row vec(E_11) vec(I)^T,
+    # so the operator is not diagonal), d = 4, cap 16
+    d, cap = 4, 16
+    inst = inputs.theta_hypercube_kron(d, 0)
+    a = tp.graph_tt(inst["adjacency"])
+    o4 = tt_ipm.TTIPM(tp.theta(a, d), tt_ipm.Options(rank_cap=cap, max_iters=40))
+    ctx = tg.Context.theta(a, tg.default_options(rank_cap=cap, max_iters=40))
+    for it in range(41):
+        info = ctx.newton_step()
+        done = o4.iterate(it) is None
+        h = o4.history[-1]
+        assert math.isclose(info["pobj"], h.pobj, rel_tol=OBJ_TOL, abs_tol=1e-9), (it, info["pobj"], h.pobj)
+        assert math.isclose(info["dobj"], h.dobj, rel_tol=OBJ_TOL, abs_tol=1e-9), (it, info["dobj"], h.dobj)
+        assert bool(info["converged"]) == done, (it, info, h)
+        if done:
+            break
+        assert ctx.ranks(0) == h.ranks_X and ctx.ranks(3) == h.ranks_Z, (it, ctx.ranks(0), h.ranks_X)
+    assert info["converged"]
+    ref = sd.solve_dense(sd.theta_sdp(inst["adjacency"]), tol=1e-10)
+    assert abs(info["pobj"] - ref.pobj) / (1 + abs(ref.pobj)) <= 1e-3
+
+
+def test_gmres_local_solves_at_real_ranks_reach_the_dense_optimum():
+    # d = 8, cap 64, every local system of more than 512 unknowns on the
+    # matrix-free GMRES path (restarted, FP64 forcing check); the result is
+    # compared with the dense optimum
+    d = 8
+    inst = inputs.maxcut_kron(d, 3)
+    ref = sd.solve_dense(sd.maxcut_sdp(inst["weights"]), tol=1e-10)
+    ctx = tg.Context.maxcut(inst["adjacency_cores"], tg.default_options(rank_cap=64, max_iters=40,
+                                                                         local_dense_max=512, time_limit=120.0))
+    res = ctx.solve()
+    assert res["status"] == 0, res
+    info = ctx.newton_step()
+    assert info["gmres_iters"] > 0
+    err = abs(res["pobj"] - ref.pobj) / (1 + abs(ref.pobj))
+    gap = abs(res["pobj"] - res["dobj"]) / (1 + abs(res["pobj"]))
+    assert err <= gap + res["rel_p"] + res["rel_d"], (err, gap, res)
