@@ -891,8 +891,8 @@ def run_micro_lu(a):
 
 
 def run_micro_contract(a):
-    """Contraction microbenchmark: one left environment update and one local
-    product (three-stage contractions, rows a6 and a7) at the shapes of the
+    """Contraction microbenchmark: one left and one right environment update
+    and one local product (three-stage contractions, rows a6 and a7) at the shapes of the
     configured workloads: frame and vector ranks r, operator ranks R, modes
     4 x 4, with (r, R) = (16, 32), (64, 128), (128, 256). CUDA events on the
     launching stream around `steps` calls after `warmup`; algorithmic flops
@@ -915,6 +915,7 @@ def run_micro_contract(a):
         flops = (2.0 * r * R * r * 4 * r + 2.0 * r * r * (R * 4) * (4 * R) + 2.0 * r * R * r * r * 4)
         for pn in ("fp64", "fp32", "tf32", "bf16"):
             for name, fn in (("env_left", lambda: tg.env_left_step(dims, phi, u, op, v, out, PREC[pn])),
+                             ("env_right", lambda: tg.env_right_step(dims, psi, u, op, v, out, PREC[pn])),
                              ("local_apply", lambda: tg.local_apply(dims, phi, op, psi, v, y, PREC[pn]))):
                 for _ in range(a.warmup):
                     fn()

@@ -185,7 +185,7 @@ static void env_left_t(const CDims& d, const T* phi, const T* u, const T* op, co
 
 template <typename T>
 static void env_right_t(const CDims& d, const T* psi, const T* u, const T* op, const T* v, T* out,
-                        T* t1, T* t2, cudaStream_t st) {
+                        T* t1, T* t2, cudaStream_t st, int prec) {
   const long long rw = d.rw, rw2 = d.rw2, R = d.R, R2 = d.R2, rv = d.rv, rv2 = d.rv2, m = d.m,
                   n = d.n;
   const size_t npsi = rw2 * R2 * rv2, nu = rw * m * rw2, nop = R * m * n * R2, nv = rv * n * rv2;
@@ -199,8 +199,10 @@ static void env_right_t(const CDims& d, const T* psi, const T* u, const T* op, c
     set_batch(g, {});
     gemm_nd<T>(g, v, nv, psi, npsi, t1, nt1, T(1), T(0), st);
   }
-  // stage 2: T2[a][p][i][b'] = sum_{j,q} Op[p][i][j][q] T1[a][j][b'][q]
-  {
+  // stage 2: T2[a][p][i][b'] = sum_{j,q} Op[p][i][j][q] T1[a][j][b'][q]; on the
+  // tensor cores T2 comes back as [(p,i)][(a,b')] and stage 3 reads it so
+  const bool tc = tc_stage2_right<T>(prec, rv, R, R2, m, n, rw2, op, t1, t2, st);
+  if (!tc) {
     GemmND g;
     set_batch(g, {{(int)rv, 0, n * rw2 * R2, R * m * rw2}});
     set_dim(g.M, g.aM, g.cM, {{(int)(R * m), n * R2, rw2}});
@@ -209,7 +211,15 @@ static void env_right_t(const CDims& d, const T* psi, const T* u, const T* op, c
     gemm_nd<T>(g, op, nop, t1, nt1, t2, nt2, T(1), T(0), st);
   }
   // stage 3: out[a'][p][a] = sum_{i,b'} U[a'][i][b'] T2[a][p][i][b']
-  {
+  if (tc) {
+    const long long nc = rv * rw2;  // row stride of the [(p,i)][(a,b')] layout
+    GemmND g;
+    set_dim(g.M, g.aM, g.cM, {{(int)rw, m * rw2, R * rv}});
+    set_dim(g.N, g.bN, g.cN, {{(int)R, m * nc, rv}, {(int)rv, rw2, 1}});
+    set_dim(g.K, g.aK, g.bK, {{(int)m, rw2, nc}, {(int)rw2, 1, 1}});
+    set_batch(g, {});
+    gemm_nd<T>(g, u, nu, t2, nt2, out, nout, T(1), T(0), st);
+  } else {
     GemmND g;
     set_dim(g.M, g.aM, g.cM, {{(int)rw, m * rw2, R * rv}});
     set_dim(g.N, g.bN, g.cN, {{(int)R, m * rw2, rv}, {(int)rv, R * m * rw2, 1}});
@@ -347,7 +357,7 @@ void env_right_step(const CDims& d, const double* psi, const double* u, const do
   stats_begin(st);
   if (prec == TT_FP64) {
     DBuf<double> t1(t1n), t2(t2n);
-    env_right_t<double>(d, psi, u, op, v, out, t1.get(), t2.get(), st);
+    env_right_t<double>(d, psi, u, op, v, out, t1.get(), t2.get(), st, prec);
   } else {
     F32Scratch s;
     s.a.alloc(sz_psi(d)); s.b.alloc(sz_u(d)); s.c.alloc(sz_op(d)); s.d.alloc(sz_v(d));
@@ -356,7 +366,7 @@ void env_right_step(const CDims& d, const double* psi, const double* u, const do
                           {(long long)sz_psi(d), (long long)sz_u(d), (long long)sz_op(d), (long long)sz_v(d)}, 4},
                     s.nrm.get(), st);
     env_right_t<float>(d, s.a.get(), s.b.get(), s.c.get(), s.d.get(), s.e.get(), s.t1.get(),
-                       s.t2.get(), st);
+                       s.t2.get(), st, prec);
     to_double_scaled(s.e.get(), out, (long long)sz_phi(d), s.nrm.get(), 4, st);
   }
   stats_end(st, contract_flops(d));

@@ -193,7 +193,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncwarp();
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
+    // the accumulator goes out through shared memory (the operand ring is idle
+    // once `done` has fired): each lane holds 32 columns of its own row after
+    // tcgen05.ld, the warp transposes them through a padded 32 x 33 buffer and
+    // then stores one row per instruction, 128 contiguous bytes
+    float* stage = reinterpret_cast<float*>(sA) + warp * 32 * 33;
 #pragma unroll 1
     for (int c0 = 0; c0 < TC_BN; c0 += 32) {
       uint32_t v[32];
@@ -209,13 +213,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        float* dst = C + (long long)row * ldc + n0 + c0;
-        const int lim = N - (n0 + c0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < lim) dst[j] = __uint_as_float(v[j]);
+      for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);
+      __syncwarp();
+      const int lim = N - (n0 + c0);
+      for (int r = 0; r < 32; ++r) {
+        const int row = m0 + warp * 32 + r;
+        if (row < M && lane < lim) C[(long long)row * ldc + n0 + c0 + lane] = stage[r * 33 + lane];
       }
+      __syncwarp();
     }
   }
   if (!ok || s_fail) {
@@ -415,6 +421,70 @@ bool tc_stage2(int prec, long long rw, long long R, long long R2, long long m, l
     return true;
   }
 }
+
+namespace {
+// [(p,i)][(j,q)] <- Op[p][i][j][q]: the natural layout with K padded to ld
+template <typename TO>
+__global__ void pack_op_right_kernel(const float* __restrict__ op, long long rows, long long K, long long ld,
+                                     TO* out) {
+  const long long tot = rows * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / ld, k = e % ld;
+    out[e] = (TO)(k < K ? op[row * K + k] : 0.f);
+  }
+}
+
+// [(a,b')][(j,q)] <- T1[a][j][b'][q], K padded to ld
+template <typename TO>
+__global__ void pack_t1_right_kernel(const float* __restrict__ t1, int rv, int n, int rw2, int R2, long long ld,
+                                     TO* out) {
+  const long long Nr = (long long)rv * rw2, tot = Nr * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / ld, k = e % ld;
+    float v = 0.f;
+    if (k < (long long)n * R2) {
+      const int a = (int)(row / rw2), b = (int)(row % rw2), j = (int)(k / R2), q = (int)(k % R2);
+      v = t1[(((long long)a * n + j) * rw2 + b) * R2 + q];
+    }
+    out[e] = (TO)v;
+  }
+}
+}  // namespace
+
+template <typename T>
+bool tc_stage2_right(int prec, long long rv, long long R, long long R2, long long m, long long n, long long rw2,
+                     const T* op, const T* t1, T* t2, cudaStream_t st) {
+  if (prec == TT_FP64 || prec == TT_FP32) return false;
+  if constexpr (!std::is_same<T, float>::value) {
+    throw TTError(TT_E_INTERNAL, "tensor-core stage needs float operands");
+  } else {
+    const bool bf16 = prec == TT_MIXED_BF16;
+    const long long M = R * m, N = rv * rw2, Kr = n * R2;
+    const long long Kp = (Kr + 7) / 8 * 8;
+    const int esz = bf16 ? 2 : 4;
+    DBuf<uint8_t> a((size_t)(M * Kp * esz)), b((size_t)(N * Kp * esz));
+    if (bf16) {
+      pack_op_right_kernel<__nv_bfloat16><<<grid1(M * Kp), 256, 0, st>>>(op, M, Kr, Kp, (__nv_bfloat16*)a.get());
+      pack_t1_right_kernel<__nv_bfloat16><<<grid1(N * Kp), 256, 0, st>>>(t1, (int)rv, (int)n, (int)rw2, (int)R2, Kp,
+                                                                          (__nv_bfloat16*)b.get());
+    } else {
+      pack_op_right_kernel<float><<<grid1(M * Kp), 256, 0, st>>>(op, M, Kr, Kp, (float*)a.get());
+      pack_t1_right_kernel<float><<<grid1(N * Kp), 256, 0, st>>>(t1, (int)rv, (int)n, (int)rw2, (int)R2, Kp,
+                                                                  (float*)b.get());
+    }
+    count_launch();
+    count_launch();
+    check_launch("tc pack (right)");
+    tc_gemm_tn(prec, (int)M, (int)N, (int)Kp, 1, a.get(), 0, b.get(), 0, t2, 0, st,
+               2.0 * (double)M * (double)N * (double)Kr);
+    return true;
+  }
+}
+
+template bool tc_stage2_right<double>(int, long long, long long, long long, long long, long long, long long,
+                                      const double*, const double*, double*, cudaStream_t);
+template bool tc_stage2_right<float>(int, long long, long long, long long, long long, long long, long long,
+                                     const float*, const float*, float*, cudaStream_t);
 
 template bool tc_stage2<double>(int, long long, long long, long long, long long, long long, long long,
                                 const double*, const double*, double*, cudaStream_t);

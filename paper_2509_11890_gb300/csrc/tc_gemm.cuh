@@ -14,6 +14,13 @@ template <typename T>
 bool tc_stage2(int prec, long long rw, long long R, long long R2, long long m, long long n,
                long long rv2, const T* op, const T* t1, T* t2, cudaStream_t st);
 
+// The middle stage of the right environment update on the tensor cores:
+//   T2[(p,i)][(a,b')] = sum_{j,q} Op[p][i][j][q] T1[a][j][b'][q]
+// (C row-major, (R m) x (rv rw2)); same contract as tc_stage2.
+template <typename T>
+bool tc_stage2_right(int prec, long long rv, long long R, long long R2, long long m, long long n, long long rw2,
+                     const T* op, const T* t1, T* t2, cudaStream_t st);
+
 // Plain tensor-core GEMM C[b] (M x N, fp32 row-major) = A[b] (M x K) * B[b] (N x K)^T,
 // both operands K-major in the given element type (TT_MIXED_TF32: fp32 storage
 // read as TF32; TT_MIXED_BF16: bf16 storage). Used by stage 2 and by the
