@@ -255,6 +255,12 @@ typedef struct {
   double nu0, nu_max;      /* first and largest relaxation nu (1e-6, 1e-3)            */
   int32_t refine_sweeps;   /* reduced precisions: FP64 sweeps that close every AMEn
                               solve (1 by default; 1..8)                           */
+  int32_t fp32_factors;    /* TT_FP64: 1 (default) lets the dense local solves factor
+                              in FP32 and refine in FP64 (mixed-precision iterative
+                              refinement), keeping the result only when its FP64
+                              relative residual reaches 1e-14; after the first miss
+                              in an AMEn solve its remaining solves factor in FP64.
+                              0: FP64 factors only                                  */
 } tt_sdp_options;
 
 typedef struct tt_sdp_ctx tt_sdp_ctx;
@@ -349,6 +355,36 @@ tt_sdp_ctx* tt_sdp_batch_member(tt_sdp_ctx* ctx, int32_t i);
  * the returned x. Synchronises the stream. */
 tt_status tt_lu_solve(int32_t n, const double* K, double* b, int32_t precision, double* rel_residual,
                       void* stream);
+
+/* Row a5 as the AMEn sweeps run it: the reduced projected system of
+ * Section 3.3 (eq. reduced_kkt_system) solved by the block elimination that
+ * follows it there. K is n x n row-major FP64 on the DEVICE (not modified),
+ * unknowns [dX; multipliers] with dX the first n_lz, equations [multiplier
+ * rows; complementarity rows] with the complementarity rows the last n_lz,
+ * so that the bottom-left n_lz x n_lz block is the projected L_Z (symmetric
+ * positive definite while Z is; only its symmetric part is factored). With
+ * L_Z = U^T U (Cholesky), the multipliers solve the Schur complement system
+ * (F - E L_Z^-1 G) dl = b_m - E L_Z^-1 b_c by LU with partial pivoting
+ * (F, E, G the remaining blocks), and dX = L_Z^-1 (b_c - G dl). Every
+ * solve is refined in FP64 against K; refinement stops at the target, after
+ * the step budget, or once a step fails to halve the residual. TT_FP64: FP32
+ * factors first (mixed-precision iterative refinement, at most eight steps
+ * towards 1e-15), kept when the relative residual reaches 1e-14; otherwise
+ * FP64 factors (at most three steps towards 1e-15). Reduced precisions: FP32
+ * factors and at most five steps towards 1e-10. When L_Z is not numerically
+ * positive definite, or the residual stays above 1e-10, the whole system is
+ * solved as tt_lu_solve does. b (n doubles, device) is overwritten by x; *rel_residual
+ * (host) receives the FP64 relative residual. 0 < n_lz < n is required.
+ * Synchronises the stream. */
+tt_status tt_kkt_solve(int32_t n, int32_t n_lz, const double* K, double* b, int32_t precision,
+                       double* rel_residual, void* stream);
+/* Block-elimination solves of tt_kkt_solve and of the AMEn sweeps completed,
+ * those of them that kept FP32 factors, those that fell back to the LU of
+ * the whole system, and the Cholesky factorisations (FP32 or FP64) that met
+ * a pivot of L_Z that was not positive, since the last reset (reset != 0
+ * clears all four after reading; any pointer may be NULL). */
+void tt_kkt_stats(uint64_t* block_solves, uint64_t* fp32_factor_solves, uint64_t* lu_fallbacks,
+                  uint64_t* lz_not_pd, int32_t reset);
 
 /* Row a9 on host data: TT rounding (Section 2.3, round_TT) followed by the
  * spectral shift of Section 3.4, Corollary psdness_rounding. `in` names HOST
@@ -487,11 +523,14 @@ void tt_contraction_stats_reset(void);
  * reset: algorithmic flops (2 M N K with the unpadded K), device seconds from
  * CUDA events around each launch, and the launch count. */
 void tt_tc_stats(double* flops, double* seconds, uint64_t* launches);
-/* Dense local solves of the AMEn sweeps (LU with partial pivoting and its
- * triangular solves, FP64, or FP32 factors with FP64 refinement) since the
- * last reset: algorithmic flops (2 N^3 / 3 per factorisation plus 2 N^2 per
- * triangular-solve pair), device seconds from CUDA events and the number of
- * local systems. Reset with tt_contraction_stats_reset. */
+/* Dense local solves of the AMEn sweeps since the last reset: algorithmic
+ * flops, device seconds from CUDA events and the number of local systems.
+ * Block elimination (N unknowns, n of them dX, m = N - n): n^3 / 3 + 2 n^2 m
+ * + 2 n m^2 + 2 m^3 / 3 per factorisation plus 4 n^2 + 2 m^2 + 4 n m per
+ * solve; LU of the whole system (the fallback, and tt_lu_solve): 2 N^3 / 3
+ * per factorisation plus 2 N^2 per triangular-solve pair (the time of a
+ * fallback includes the block attempt). Reset with
+ * tt_contraction_stats_reset. */
 void tt_lu_stats(double* flops, double* seconds, uint64_t* calls);
 /* Per-phase host wall time accumulated while the environment variable
  * TTSDP_PROFILE=1 is set (each phase then synchronises the stream): one

@@ -559,3 +559,25 @@ def lu_solve(K, b, precision=FP64, stream=None) -> float:
     _check(lib().tt_lu_solve(n, _ptr(K), _ptr(b), int(precision), ctypes.byref(res), _stream(stream)),
            "tt_lu_solve")
     return res.value
+
+
+def kkt_solve(K, b, n_lz: int, precision=FP64, stream=None) -> float:
+    """tt_kkt_solve: b (device, float64) <- K^{-1} b for a reduced projected
+    system K (n x n, float64, row-major, kept) whose last n_lz rows and first
+    n_lz columns hold the positive definite L_Z block, by block elimination;
+    returns the FP64 relative residual."""
+    n = int(K.shape[0])
+    assert K.shape == (n, n) and b.numel() == n
+    res = ctypes.c_double(0.0)
+    _check(lib().tt_kkt_solve(n, int(n_lz), _ptr(K), _ptr(b), int(precision), ctypes.byref(res),
+                              _stream(stream)), "tt_kkt_solve")
+    return res.value
+
+
+def kkt_stats(reset: bool = False, not_pd: bool = False):
+    """(block-elimination solves, of them with FP32 factors, LU fallbacks)
+    since the last reset, and with not_pd=True also the Cholesky
+    factorisations that met a non-positive pivot of L_Z."""
+    a, h, f, z = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    lib().tt_kkt_stats(ctypes.byref(a), ctypes.byref(h), ctypes.byref(f), ctypes.byref(z), int(bool(reset)))
+    return (a.value, h.value, f.value, z.value) if not_pd else (a.value, h.value, f.value)

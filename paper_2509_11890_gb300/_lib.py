@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("eig_rank", c_int32), ("eig_sweeps", c_int32), ("seed", ctypes.c_uint64),
                 ("local_dense_max", c_int32), ("gmres_restart", c_int32), ("gmres_max_iters", c_int32),
                 ("eig_two_site", c_int32), ("time_limit", c_double), ("combined_multipliers", c_int32),
-                ("finish_tol", c_double), ("nu0", c_double), ("nu_max", c_double), ("refine_sweeps", c_int32)]
+                ("finish_tol", c_double), ("nu0", c_double), ("nu_max", c_double), ("refine_sweeps", c_int32),
+                ("fp32_factors", c_int32)]
 
 
 class IterInfo(ctypes.Structure):
@@ -94,6 +95,9 @@ SIGNATURES = {
     "tt_sdp_batch_size": (c_int32, [c_void_p]),
     "tt_sdp_batch_member": (c_void_p, [c_void_p, c_int32]),
     "tt_lu_solve": (c_int32, [c_int32, c_void_p, c_void_p, c_int32, P_double, c_void_p]),
+    "tt_kkt_solve": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_int32, P_double, c_void_p]),
+    "tt_kkt_stats": (None, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                            ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), c_int32]),
     "tt_sdp_round": (c_int32, [ctypes.POINTER(TTDesc), c_double, c_int32, c_int32, ctypes.POINTER(TTDesc), P_double,
                                c_void_p]),
     "tt_sdp_create_maxcut": (c_int32, [ctypes.POINTER(TTDesc), ctypes.POINTER(Options), c_void_p,

@@ -114,6 +114,8 @@ Options to_options(const tt_sdp_options* o) {
   r.nu0 = o->nu0;
   r.nu_max = o->nu_max;
   r.refine_sweeps = o->refine_sweeps;
+  r.fp32_factors = o->fp32_factors;
+  TT_CHECK(r.fp32_factors == 0 || r.fp32_factors == 1, TT_E_INVALID_ARG, "fp32_factors must be 0 or 1");
   TT_CHECK(r.refine_sweeps >= 1 && r.refine_sweeps <= 8, TT_E_INVALID_ARG, "refine_sweeps must be in 1..8");
   TT_CHECK(r.finish_tol >= 0.0 && r.nu0 > 0.0 && r.nu_max >= r.nu0, TT_E_INVALID_ARG,
            "finishing phase: finish_tol >= 0 and 0 < nu0 <= nu_max");
@@ -331,6 +333,28 @@ tt_status tt_lu_solve(int32_t n, const double* K, double* b, int32_t precision, 
   });
 }
 
+tt_status tt_kkt_solve(int32_t n, int32_t n_lz, const double* K, double* b, int32_t precision,
+                       double* rel_residual, void* stream) {
+  return guarded(stream, [&] {
+    TT_CHECK(n > 0 && n_lz > 0 && n_lz < n && K && b && rel_residual, TT_E_INVALID_ARG,
+             "bad tt_kkt_solve arguments");
+    TT_CHECK(precision >= TT_FP64 && precision <= TT_MIXED_BF16, TT_E_INVALID_ARG, "unknown precision");
+    int corr = 0;
+    *rel_residual = dense_local_solve(precision, n, const_cast<double*>(K), b, &corr, n_lz);
+    TT_CUDA(sync_stream(cur_stream()));
+  });
+}
+
+void tt_kkt_stats(uint64_t* block_solves, uint64_t* fp32_factor_solves, uint64_t* lu_fallbacks,
+                  uint64_t* lz_not_pd, int32_t reset) {
+  unsigned long long a = 0, h = 0, f = 0, z = 0;
+  kkt_counts(&a, &h, &f, &z, reset != 0);
+  if (block_solves) *block_solves = a;
+  if (fp32_factor_solves) *fp32_factor_solves = h;
+  if (lu_fallbacks) *lu_fallbacks = f;
+  if (lz_not_pd) *lz_not_pd = z;
+}
+
 tt_status tt_sdp_round(const tt_desc* in, double tol, int32_t rank_cap, int32_t psd_shift, tt_desc* out,
                        double* zeta_out, void* stream) {
   return guarded(stream, [&] {
@@ -401,6 +425,7 @@ void tt_sdp_default_options(tt_sdp_options* o) {
   o->nu0 = 1e-6;
   o->nu_max = 1e-3;
   o->refine_sweeps = 1;
+  o->fp32_factors = 1;
 }
 
 }  // extern "C"

@@ -917,6 +917,24 @@ void qr_thin(MatView<T> A, T* Q, T* R, cudaStream_t st) {
   check_launch("qr_kernel");
 }
 
+// out = X made orthonormal by two Newton-Schulz steps X <- X (3 I - X^T X) / 2
+// (X n x n, out distinct from X). With delta = ||X^T X - I|| one step leaves
+// about 1.5 delta^2 and two about 3.4 delta^4: from an FP32-accurate X (delta
+// ~ 1e-6) one step would leave ~1e-12, which shows in every reconstruction
+// B = W V^T made with it; two reach FP64 rounding.
+static void ns_orthonormalise(int n, const double* X, double* out, cudaStream_t st) {
+  DBuf<double> G((size_t)n * n), Y((size_t)n * n);
+  const double* cur = X;
+  for (int step = 0; step < 2; ++step) {
+    double* dst = step == 1 ? out : Y.get();
+    gemm_rm<double>(true, false, n, n, n, 1.0, cur, n, 0, cur, n, 0, 0.0, G.get(), n, 0, 1, st);
+    newton_schulz_rhs_kernel<<<grid_for((long long)n * n), 256, 0, st>>>(G.get(), n);
+    count_launch();
+    gemm_rm<double>(false, false, n, n, n, 1.0, cur, n, 0, G.get(), n, 0, 0.0, dst, n, 0, 1, st);
+    cur = dst;
+  }
+}
+
 // Finishes the SVD of B from W = B V (V orthonormal, W's columns nearly
 // orthogonal) by first-order Jacobi steps computed from the Gram matrix with
 // multi-CTA GEMMs: each step rotates by J = orth(I + K) (K from
@@ -961,11 +979,8 @@ bool first_order_finish(DBuf<double>& W, DBuf<double>& V, int m, int n, bool tra
       break;
     }
     if (!(maxang <= kMaxAngle)) return false;
-    // J <- J (3 I - J^T J) / 2, then W <- W J, V <- V J
-    gemm_rm<double>(true, false, n, n, n, 1.0, J.get(), n, 0, J.get(), n, 0, 0.0, G.get(), n, 0, 1, st);
-    newton_schulz_rhs_kernel<<<grid_for((long long)n * n), 256, 0, st>>>(G.get(), n);
-    count_launch();
-    gemm_rm<double>(false, false, n, n, n, 1.0, J.get(), n, 0, G.get(), n, 0, 0.0, H.get(), n, 0, 1, st);
+    // H = J made orthonormal, then W <- W H, V <- V H
+    ns_orthonormalise(n, J.get(), H.get(), st);
     gemm_rm<double>(false, false, m, n, n, 1.0, W.get(), n, 0, H.get(), n, 0, 0.0, W2.get(), n, 0, 1, st);
     gemm_rm<double>(false, false, n, n, n, 1.0, V.get(), n, 0, H.get(), n, 0, 0.0, V2.get(), n, 0, 1, st);
     std::swap(W, W2);
@@ -1048,14 +1063,11 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st, SvdSide side) {
       convert_kernel<double, float><<<grid_for((long long)m * n), 256, 0, st>>>(B64.get(), (long long)m * n, B32.get());
       count_launch();
       svd_thin<float>(MatView<float>{B32.get(), m, n, n, 1}, U32.get(), S32.get(), Vt32.get(), st);
-      // V0 = Vt32^T in FP64, then one Newton-Schulz step V0 (3 I - V0^T V0) / 2
+      // V0 = Vt32^T in FP64, made orthonormal by Newton-Schulz steps
       transpose<float>(n, n, Vt32.get(), U32.get(), st);
       convert_kernel<float, double><<<grid_for((long long)n * n), 256, 0, st>>>(U32.get(), (long long)n * n, H.get());
       count_launch();
-      gemm_rm<double>(true, false, n, n, n, 1.0, H.get(), n, 0, H.get(), n, 0, 0.0, G.get(), n, 0, 1, st);
-      newton_schulz_rhs_kernel<<<grid_for((long long)n * n), 256, 0, st>>>(G.get(), n);
-      count_launch();
-      gemm_rm<double>(false, false, n, n, n, 1.0, H.get(), n, 0, G.get(), n, 0, 0.0, V0.get(), n, 0, 1, st);
+      ns_orthonormalise(n, H.get(), V0.get(), st);
       gemm_rm<double>(false, false, m, n, n, 1.0, B64.get(), n, 0, V0.get(), n, 0, 0.0, W.get(), n, 0, 1, st);
       check_launch("svd preconditioning");
       if (first_order_finish(W, V0, m, n, tr, need_v, U, S, Vt, st)) return;
@@ -1149,9 +1161,191 @@ void lu_factor(int n, T* A, int* ipiv, cudaStream_t st) {
   check_launch("lu_factor");
 }
 
+namespace {
+
+// Rows of one step of the cluster triangular solves, and the cluster size.
+constexpr int kApplyNB = 64;
+constexpr int kApplyCtas = 8;
+constexpr int kApplyThreads = 512;
+
+// The solves of lu_apply_kernel spread over a cluster of kApplyCtas CTAs:
+// U^T y = b by 64-row steps from the top, then L^T z = y from the bottom,
+// then x[i] = z[perm[i]] (perm null: x = z). In each step every CTA loads
+// the step's 64 x 64 diagonal triangle into shared memory and solves it in
+// one warp (two unknowns per lane) from the step's right-hand side, which the
+// previous steps have completed; CTA 0 stores the step's unknowns, and every
+// warp of the cluster subtracts their contribution from the rows it owns
+// below (forward) or above (backward) the step, one row per warp at a time
+// with the 64 products in its lanes. One cluster barrier (hardware, with
+// release / acquire ordering of the CTAs' global writes) ends each step, so
+// no step reads a right-hand side entry another CTA is still updating.
+// b is the right-hand side on entry (updated in place by the forward steps)
+// and x on exit; y and w are n-entry scratch vectors. Entries that another
+// CTA wrote are read and written at L2 (ld/st.cg), past the SM's L1.
 template <typename T>
-void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st) {
+__global__ void __launch_bounds__(kApplyThreads) lu_apply_cluster_kernel(int n, const T* __restrict__ B,
+                                                                         const int* __restrict__ perm, T* b, T* y,
+                                                                         T* w) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  __shared__ T tri[kApplyNB][kApplyNB + 1];
+  __shared__ T xb[kApplyNB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarpsPerCta = kApplyThreads / 32;
+  const int gwarp = rank * kWarpsPerCta + warp, nwarps = kApplyCtas * kWarpsPerCta;
+  // forward: U^T y = b (lower triangle of the buffer, diagonal included)
+  for (int i0 = 0; i0 < n; i0 += kApplyNB) {
+    const int ib = n - i0 < kApplyNB ? n - i0 : kApplyNB, i1 = i0 + ib;
+    for (int e = tid; e < ib * ib; e += kApplyThreads) {
+      const int r = e / ib, c = e % ib;
+      if (c <= r) tri[r][c] = B[(long long)(i0 + r) * n + i0 + c];
+    }
+    if (tid < ib) xb[tid] = __ldcg(b + i0 + tid);
+    __syncthreads();
+    if (warp == 0) {
+      T v0 = lane < ib ? xb[lane] : T(0), v1 = lane + 32 < ib ? xb[lane + 32] : T(0);
+      for (int t = 0; t < ib; ++t) {
+        T xt;
+        if (t < 32) {
+          if (lane == t) v0 = tri[t][t] != T(0) ? v0 / tri[t][t] : T(0);
+          xt = __shfl_sync(0xffffffffu, v0, t);
+        } else {
+          if (lane == t - 32) v1 = tri[t][t] != T(0) ? v1 / tri[t][t] : T(0);
+          xt = __shfl_sync(0xffffffffu, v1, t - 32);
+        }
+        if (lane > t && lane < ib) v0 -= tri[lane][t] * xt;
+        if (lane + 32 > t && lane + 32 < ib) v1 -= tri[lane + 32][t] * xt;
+      }
+      if (lane < ib) xb[lane] = v0;
+      if (lane + 32 < ib) xb[lane + 32] = v1;
+    }
+    __syncthreads();
+    if (rank == 0 && tid < ib) __stcg(y + i0 + tid, xb[tid]);
+    for (int row = i1 + gwarp; row < n; row += nwarps) {
+      const T* Br = B + (long long)row * n + i0;
+      T s = (lane < ib ? Br[lane] * xb[lane] : T(0)) + (lane + 32 < ib ? Br[lane + 32] * xb[lane + 32] : T(0));
+      s = warp_sum(s);
+      if (lane == 0) __stcg(b + row, __ldcg(b + row) - s);
+    }
+    cluster.sync();
+  }
+  // backward: L^T z = y (strict upper triangle of the buffer, unit diagonal)
+  for (int i1 = n; i1 > 0;) {
+    const int i0 = i1 - kApplyNB > 0 ? i1 - kApplyNB : 0, ib = i1 - i0;
+    for (int e = tid; e < ib * ib; e += kApplyThreads) {
+      const int r = e / ib, c = e % ib;
+      if (c > r) tri[r][c] = B[(long long)(i0 + r) * n + i0 + c];
+    }
+    if (tid < ib) xb[tid] = __ldcg(y + i0 + tid);
+    __syncthreads();
+    if (warp == 0) {
+      T v0 = lane < ib ? xb[lane] : T(0), v1 = lane + 32 < ib ? xb[lane + 32] : T(0);
+      for (int t = ib - 1; t > 0; --t) {
+        const T xt = t < 32 ? __shfl_sync(0xffffffffu, v0, t) : __shfl_sync(0xffffffffu, v1, t - 32);
+        if (lane < t) v0 -= tri[lane][t] * xt;
+        if (lane + 32 < t) v1 -= tri[lane + 32][t] * xt;
+      }
+      if (lane < ib) xb[lane] = v0;
+      if (lane + 32 < ib) xb[lane + 32] = v1;
+    }
+    __syncthreads();
+    if (rank == 0 && tid < ib) __stcg(w + i0 + tid, xb[tid]);
+    for (int row = gwarp; row < i0; row += nwarps) {
+      const T* Br = B + (long long)row * n + i0;
+      T s = (lane < ib ? Br[lane] * xb[lane] : T(0)) + (lane + 32 < ib ? Br[lane + 32] * xb[lane + 32] : T(0));
+      s = warp_sum(s);
+      if (lane == 0) __stcg(y + row, __ldcg(y + row) - s);
+    }
+    cluster.sync();
+    i1 = i0;
+  }
+  // x = P^T z as a gather
+  for (int i = rank * kApplyThreads + tid; i < n; i += kApplyCtas * kApplyThreads)
+    __stcg(b + i, __ldcg(w + (perm ? perm[i] : i)));
+}
+
+// perm[i] = the index the interchanges ipiv of lu_factor (applied in reverse
+// order, as lu_apply_kernel applies them) move to position i; one thread
+// composes them in shared memory.
+__global__ void lu_perm_kernel(int n, const int* __restrict__ ipiv, int* __restrict__ perm) {
+  extern __shared__ int perm_smem[];
+  int* p = perm_smem;
+  int* piv = perm_smem + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    p[i] = i;
+    piv[i] = ipiv[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int j = n - 1; j >= 0; --j) {
+      const int q = piv[j];
+      if (q != j) {
+        const int t = p[j];
+        p[j] = p[q];
+        p[q] = t;
+      }
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = p[i];
+}
+
+}  // namespace
+
+void lu_perm(int n, const int* ipiv, int* perm, cudaStream_t st) {
   if (n <= 0) return;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(lu_perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  TT_CUDA(attr_err);
+  TT_CHECK((size_t)n * 2 * sizeof(int) <= 200 * 1024, TT_E_INVALID_ARG, "lu_perm: system too large");
+  lu_perm_kernel<<<1, 256, (size_t)n * 2 * sizeof(int), st>>>(n, ipiv, perm);
+  count_launch();
+  check_launch("lu_perm");
+}
+
+namespace {
+
+// Systems from this size on are solved by the cluster kernel.
+constexpr int kApplyClusterMin = 160;
+
+template <typename T>
+void lu_apply_cluster(int n, const T* LU, const int* perm, T* b, cudaStream_t st) {
+  DBuf<T> y((size_t)n), w((size_t)n);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kApplyCtas, 1, 1);
+  cfg.blockDim = dim3(kApplyThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kApplyCtas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  TT_CUDA(cudaLaunchKernelEx(&cfg, lu_apply_cluster_kernel<T>, n, LU, perm, b, y.get(), w.get()));
+  count_launch();
+  check_launch("lu_apply_cluster_kernel");
+}
+
+}  // namespace
+
+template <typename T>
+void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st, const int* perm) {
+  if (n <= 0) return;
+  if (n >= kApplyClusterMin) {
+    if (perm) {
+      lu_apply_cluster<T>(n, LU, perm, b, st);
+    } else {
+      DBuf<int> p((size_t)n);
+      lu_perm(n, ipiv, p.get(), st);
+      lu_apply_cluster<T>(n, LU, p.get(), b, st);
+    }
+    return;
+  }
   // the solution vector in shared memory (opt-in limit, beside the kernel's
   // static 32 x 33 triangle) when it fits
   constexpr size_t kMaxSmem = 160 * 1024;
@@ -1207,7 +1401,7 @@ void transpose(int m, int n, const T* in, T* out, cudaStream_t st) {
   template void svd_thin<T>(MatView<T>, T*, T*, T*, cudaStream_t, SvdSide);     \
   template void lu_solve<T>(int, T*, T*, cudaStream_t);                         \
   template void lu_factor<T>(int, T*, int*, cudaStream_t);                      \
-  template void lu_solve_factored<T>(int, const T*, const int*, T*, cudaStream_t); \
+  template void lu_solve_factored<T>(int, const T*, const int*, T*, cudaStream_t, const int*); \
   template void cholesky_lower<T>(int, T*, cudaStream_t, int*);                 \
   template void tri_lower_inverse<T>(int, T*, cudaStream_t);                    \
   template void transpose<T>(int, int, const T*, T*, cudaStream_t);

@@ -41,10 +41,17 @@ void lu_solve(int n, T* A, T* b, cudaStream_t st);
 // column-major: the buffer read row-major holds L^T and U^T; interchanges in
 // ipiv, n entries); lu_solve_factored then solves A x = b in place for one
 // right-hand side and may be called any number of times on the same factors.
+// Systems of 160 unknowns or more are solved by a cluster of eight CTAs in
+// 64-row steps; perm (from lu_perm, or any array giving the final order when
+// the interchanges are known otherwise) saves composing the interchanges on
+// every call.
 template <typename T>
 void lu_factor(int n, T* A, int* ipiv, cudaStream_t st);
 template <typename T>
-void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st);
+void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st, const int* perm = nullptr);
+// perm[i] = the row of the solution of the permuted system that lands at
+// position i: the interchanges ipiv of lu_factor composed (n <= 25600).
+void lu_perm(int n, const int* ipiv, int* perm, cudaStream_t st);
 
 // Lower Cholesky factor in place (row-major n x n; upper part zeroed) and
 // the inverse of a lower triangular matrix in place. Single CTA.

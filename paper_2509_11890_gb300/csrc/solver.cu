@@ -16,6 +16,7 @@
 
 #include "contract.cuh"
 #include "gemm.cuh"
+#include "kkt.cuh"
 #include "linalg.cuh"
 #include "solver.cuh"
 #include "tc_gemm.cuh"
@@ -248,54 +249,164 @@ void svd_prec(int prec, MatView<double> A, double* U, double* S, double* Vt, cud
 // (the accuracy of an FP64 LU of the projected system)
 constexpr double kLuRefineTol = 1e-10;
 
+// Block-elimination solves that ran to the end, those of them that used FP32
+// factors, and those that fell back to the LU of the whole system (LZ block
+// not positive definite, or a residual above the tolerance after the
+// corrections).
+std::atomic<unsigned long long> g_kkt_block{0}, g_kkt_fp32{0}, g_kkt_fallback{0}, g_kkt_not_pd{0};
+
+// Block elimination with FP64 iterative refinement (factors of type T): x
+// from b, *rho the final FP64 relative residual. The corrections stop at
+// `target`, after max_corr of them, or once one fails to halve the residual
+// (the FP64 residual has reached its rounding floor, or the factors are too
+// far from K for the refinement to converge). Returns false, leaving x
+// unspecified, when the LZ block does not factor. *flops accumulates the
+// algorithmic work.
+template <typename T>
+bool kkt_refined(int N, int n, const double* K, const double* b, double* x, double* r, double bnorm, double target,
+                 int max_corr, int* corrections, double* rho, double* flops, cudaStream_t st) {
+  KktFactors<T> f;
+  *flops += kkt_factor_flops(N, n);
+  if (!kkt_factor<T>(N, n, K, f, st)) {
+    g_kkt_not_pd.fetch_add(1, std::memory_order_relaxed);
+    return false;
+  }
+  auto residual = [&]() {
+    dev_copy(r, b, N, st);
+    gemm_rm<double>(false, false, N, 1, N, -1.0, K, N, 0, x, 1, 0, 1.0, r, 1, 0, 1, st);
+    return bnorm > 0 ? dev_norm(r, N) / bnorm : 0.0;
+  };
+  kkt_apply<T>(f, K, b, x, st);
+  *flops += kkt_apply_flops(N, n);
+  *rho = residual();
+  DBuf<double> dx(N);
+  for (int c = 0; c < max_corr && *rho > target; ++c) {
+    kkt_apply<T>(f, K, r, dx.get(), st);
+    *flops += kkt_apply_flops(N, n);
+    dev_axpy(x, dx.get(), N, 1.0, st);
+    if (corrections) ++*corrections;
+    const double prev = *rho;
+    *rho = residual();
+    if (*rho > 0.5 * prev) break;
+  }
+  return true;
+}
+
+// FP64 solves by block elimination refine towards this relative residual
+// (below what an FP64 LU with partial pivoting leaves on these systems) and
+// accept FP32 factors only when the refinement gets to kFp64Accept.
+constexpr double kFp64Target = 1e-15;
+constexpr double kFp64Accept = 1e-14;
+
+// FP32 LU of the whole system with FP64 iterative refinement: x from b (x
+// starts at 0), corrections until `target`, max_corr solves, or a solve that
+// fails to halve the residual; *rho the final FP64 relative residual.
+void lu_refined_f32(int N, const double* K, const double* b, double* x, double* r, double bnorm, double target,
+                    int max_solves, int* corrections, double* rho, double* flops, cudaStream_t st) {
+  const size_t nn = (size_t)N * N;
+  DBuf<float> kf(nn), rf(N);
+  DBuf<int> ipiv(N), perm(N);
+  DBuf<double> dx(N);
+  dev_fill(x, N, 0.0, st);
+  dev_copy(r, b, N, st);
+  to_f32(K, kf.get(), nn, st);
+  lu_factor<float>(N, kf.get(), ipiv.get(), st);
+  lu_perm(N, ipiv.get(), perm.get(), st);
+  *flops += 2.0 / 3.0 * (double)N * N * N;
+  double prev = 1.0;
+  for (int it = 0; it < max_solves; ++it) {
+    to_f32(r, rf.get(), N, st);
+    lu_solve_factored<float>(N, kf.get(), ipiv.get(), rf.get(), st, perm.get());
+    *flops += 2.0 * (double)N * N;
+    to_f64(rf.get(), dx.get(), N, st);
+    dev_axpy(x, dx.get(), N, 1.0, st);
+    if (corrections && it > 0) ++*corrections;
+    dev_copy(r, b, N, st);
+    gemm_rm<double>(false, false, N, 1, N, -1.0, K, N, 0, x, 1, 0, 1.0, r, 1, 0, 1, st);
+    *rho = bnorm > 0 ? dev_norm(r, N) / bnorm : 0.0;
+    if (*rho <= target || (it > 0 && *rho > 0.5 * prev)) break;
+    prev = *rho;
+  }
+}
+
 // Solves K x = b (K N x N row-major FP64, kept; b becomes x) and returns the
-// FP64 relative residual ||b - K x|| / ||b|| of the returned x. FP64: LU of
-// a copy. Mixed modes: one FP32 LU, then FP64 iterative refinement whose
-// correction solves reuse the factors, until the FP64 residual is at most
-// ftol ||b|| or five corrections have run.
-double lu_solve_prec(int prec, int N, double* K, double* b, double ftol, int* corrections) {
+// FP64 relative residual ||b - K x|| / ||b|| of the returned x. Every path
+// refines in FP64 against K.
+// n_lz > 0: K is a reduced projected system whose last n_lz rows and first
+// n_lz columns hold the LZ block; it is solved by block elimination (Cholesky
+// of LZ, LU of the multipliers' Schur complement):
+//   FP64: FP32 factors first (while *fp32_ok), as in mixed-precision
+//   iterative refinement, kept when the FP64 residual gets to kFp64Accept;
+//   when that refinement falls short, *fp32_ok becomes false (the rest of
+//   the caller's solves go straight to FP64 factors) and FP64 factors,
+//   refined towards kFp64Target (at most three corrections), are kept at a
+//   residual <= ftol.
+//   Reduced precisions: FP32 factors, at most five corrections, kept at a
+//   residual <= ftol.
+// When LZ is not positive definite (its first Cholesky factorisation, FP32
+// or FP64, meets a pivot <= 0), the residual stays above those levels, or
+// n_lz = 0, the whole system is solved by LU with partial pivoting:
+//   FP64: FP32 factors refined as above while *fp32_ok (kept at
+//   kFp64Accept), else FP64 factors of a copy.
+//   Reduced precisions: FP32 factors and at most five FP64 refinement
+//   solves towards ftol.
+double lu_solve_prec(int prec, int N, double* K, double* b, double ftol, int* corrections, int n_lz,
+                     bool* fp32_ok) {
   cudaStream_t st = cur_stream();
-  // timed as one unit: factorisation 2 N^3 / 3 flops, every solve 2 N^2
+  // timed as one unit: the factorisations and every triangular-solve pair
   stats_begin(st, 2);
-  int nsolve = 0;
   const size_t nn = (size_t)N * N;
   const double bnorm = dev_norm(b, N);
   DBuf<double> x(N), r(N);
-  auto residual = [&]() {
-    dev_copy(r.get(), b, N, st);
-    gemm_rm<double>(false, false, N, 1, N, -1.0, K, N, 0, x.get(), 1, 0, 1.0, r.get(), 1, 0, 1, st);
-    return bnorm > 0 ? dev_norm(r.get(), N) / bnorm : 0.0;
+  double rho = 0.0, flops = 0.0;
+  const bool try32 = prec != TT_FP64 || (fp32_ok && *fp32_ok);
+  auto finish = [&]() {
+    dev_copy(b, x.get(), N, st);
+    stats_end(st, flops, 2);
+    return rho;
   };
-  double rho = 0.0;
-  if (prec == TT_FP64) {
-    DBuf<double> Kc(nn);
-    dev_copy(Kc.get(), K, nn, st);
-    dev_copy(x.get(), b, N, st);
-    lu_solve<double>(N, Kc.get(), x.get(), st);
-    ++nsolve;
-    rho = residual();
-  } else {
-    DBuf<float> kf(nn), rf(N);
-    DBuf<int> ipiv(N);
-    DBuf<double> dx(N);
-    dev_fill(x.get(), N, 0.0, st);
-    dev_copy(r.get(), b, N, st);
-    to_f32(K, kf.get(), nn, st);
-    lu_factor<float>(N, kf.get(), ipiv.get(), st);
-    for (int it = 0; it < 5; ++it) {
-      to_f32(r.get(), rf.get(), N, st);
-      lu_solve_factored<float>(N, kf.get(), ipiv.get(), rf.get(), st);
-      ++nsolve;
-      to_f64(rf.get(), dx.get(), N, st);
-      dev_axpy(x.get(), dx.get(), N, 1.0, st);
-      if (corrections && it > 0) ++*corrections;
-      rho = residual();
-      if (rho <= ftol) break;
+  if (n_lz > 0 && n_lz < N) {
+    int corr = 0;
+    bool ok = false, factored = true;
+    if (prec == TT_FP64) {
+      if (try32) {
+        factored = kkt_refined<float>(N, n_lz, K, b, x.get(), r.get(), bnorm, kFp64Target, 8, &corr, &rho, &flops,
+                                      st);
+        ok = factored && rho <= kFp64Accept;
+        if (factored && !ok) *fp32_ok = false;
+        if (ok) g_kkt_fp32.fetch_add(1, std::memory_order_relaxed);
+      }
+      if (!ok && factored)
+        ok = kkt_refined<double>(N, n_lz, K, b, x.get(), r.get(), bnorm, kFp64Target, 3, &corr, &rho, &flops, st) &&
+             rho <= ftol;
+    } else {
+      ok = kkt_refined<float>(N, n_lz, K, b, x.get(), r.get(), bnorm, ftol, 5, &corr, &rho, &flops, st) &&
+           rho <= ftol;
+      if (ok) g_kkt_fp32.fetch_add(1, std::memory_order_relaxed);
     }
+    if (corrections) *corrections += corr;
+    if (ok) {
+      g_kkt_block.fetch_add(1, std::memory_order_relaxed);
+      return finish();
+    }
+    g_kkt_fallback.fetch_add(1, std::memory_order_relaxed);
   }
-  dev_copy(b, x.get(), N, st);
-  stats_end(st, 2.0 / 3.0 * (double)N * N * N + 2.0 * (double)N * N * nsolve, 2);
-  return rho;
+  if (try32) {
+    const bool fp64 = prec == TT_FP64;
+    lu_refined_f32(N, K, b, x.get(), r.get(), bnorm, fp64 ? kFp64Target : ftol, fp64 ? 9 : 5, corrections, &rho,
+                   &flops, st);
+    if (!fp64 || rho <= kFp64Accept) return finish();
+    *fp32_ok = false;
+  }
+  DBuf<double> Kc(nn);
+  dev_copy(Kc.get(), K, nn, st);
+  dev_copy(x.get(), b, N, st);
+  lu_solve<double>(N, Kc.get(), x.get(), st);
+  flops += 2.0 / 3.0 * (double)N * N * N + 2.0 * (double)N * N;
+  dev_copy(r.get(), b, N, st);
+  gemm_rm<double>(false, false, N, 1, N, -1.0, K, N, 0, x.get(), 1, 0, 1.0, r.get(), 1, 0, 1, st);
+  rho = bnorm > 0 ? dev_norm(r.get(), N) / bnorm : 0.0;
+  return finish();
 }
 
 // ---------------------------------------------------------------------------
@@ -439,7 +550,10 @@ double move_tol(double tol, int prec) { return std::max(tol, sweep_floor(prec));
 BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap, int kick, int max_sweeps,
                    Counter& rnd, int prec_in, int dense_max, int gmres_restart, int gmres_maxit, AmenInfo* info,
                    BlockTT* warm, const std::chrono::steady_clock::time_point* deadline,
-                   int refine_sweeps = kRefineSweeps) {
+                   int refine_sweeps = kRefineSweeps, bool fp32_factors = true) {
+  // FP64 dense local solves try FP32 factors until one of them does not
+  // refine to the FP64 level; the rest of this solve then factors in FP64
+  bool fp32_ok = fp32_factors;
   // sweeps run in prec_in until they stall at its floor (or use the sweep
   // budget), then up to kRefineSweeps FP64 sweeps refine the direction with
   // FP64 environments, local operators and solves
@@ -618,7 +732,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         ps_part.reset();
         ProfScope ps_lu("dense.lu");
         int corr = 0;
-        const double rho = lu_solve_prec(prec, (int)N, K.get(), b.get(), kLuRefineTol, &corr);
+        const double rho = lu_solve_prec(prec, (int)N, K.get(), b.get(), kLuRefineTol, &corr, (int)n, &fp32_ok);
         info->forcing = std::max(info->forcing, rho);
         info->corrections += corr;
       }
@@ -661,9 +775,12 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
         // the SVD only chooses the next frame's subspace: it runs in the solve's
         // reduced precision even in the FP64 refinement sweep
+        std::optional<ProfScope> ps_svd;
+        ps_svd.emplace("move.svd");
         svd_prec(prec_in, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
                  kSvdLeft);
         std::vector<double> hs = host_copy(S.get(), kk);
+        ps_svd.reset();
         int keep = truncation_rank_rel(hs, move_tol(tol, prec) / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(rows - keep, std::max(cap - keep, 0)));
         int nk = keep + std::max(extra, 0);
@@ -700,15 +817,19 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         frame.c[k + 1] = c1;
         block = nb2;
         blockshape = {nk, 4, r3};
+        ProfScope ps_env("move.env");
         for_all([&](Env& e) { e.push_left(frame, k, prec); });
       } else {
         ProfScope ps("amen.move_bwd");
         const int rows = nblk * rl, cols = 4 * rr;
         int kk = std::min(rows, cols);
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
+        std::optional<ProfScope> ps_svd;
+        ps_svd.emplace("move.svd");
         svd_prec(prec_in, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
                  kSvdRight);
         std::vector<double> hs = host_copy(S.get(), kk);
+        ps_svd.reset();
         int keep = truncation_rank_rel(hs, move_tol(tol, prec) / std::sqrt((double)d), cap);
         int extra = std::min(kick, std::min(cols - keep, std::max(cap - keep, 0)));
         int nk = keep + std::max(extra, 0);
@@ -747,6 +868,7 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         frame.c[k - 1] = c1;
         block = nb2;
         blockshape = {rp, 4, nk};
+        ProfScope ps_env("move.env");
         for_all([&](Env& e) { e.push_right(frame, k, prec); });
       }
     }
@@ -830,8 +952,25 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
 
 }  // namespace
 
-double dense_local_solve(int prec, int N, double* K, double* b, int* corrections) {
-  return lu_solve_prec(prec, N, K, b, kLuRefineTol, corrections);
+double dense_local_solve(int prec, int N, double* K, double* b, int* corrections, int n_lz) {
+  // FP32 factors in FP64 mode for the reduced systems only: a general system
+  // is factored in FP64
+  bool fp32_ok = n_lz > 0;
+  return lu_solve_prec(prec, N, K, b, kLuRefineTol, corrections, n_lz, &fp32_ok);
+}
+
+void kkt_counts(unsigned long long* block, unsigned long long* fp32, unsigned long long* fallback,
+                unsigned long long* not_pd, bool reset) {
+  if (block) *block = g_kkt_block.load();
+  if (fp32) *fp32 = g_kkt_fp32.load();
+  if (fallback) *fallback = g_kkt_fallback.load();
+  if (not_pd) *not_pd = g_kkt_not_pd.load();
+  if (reset) {
+    g_kkt_block = 0;
+    g_kkt_fp32 = 0;
+    g_kkt_fallback = 0;
+    g_kkt_not_pd = 0;
+  }
 }
 
 DTT BlockTT::component(int b) const {
@@ -1364,7 +1503,7 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
   BlockTT warm;
   BlockTT w = amen_solve(nd, d, w_ ? w_.get() : nullptr, eta_, o_.rank_cap, o_.kick, o_.max_sweeps, rnd_,
                          o_.prec, o_.local_dense_max, o_.gmres_restart, o_.gmres_max_iters, &info, &warm,
-                         has_deadline_ ? &deadline_ : nullptr, o_.refine_sweeps);
+                         has_deadline_ ? &deadline_ : nullptr, o_.refine_sweeps, o_.fp32_factors != 0);
   gmres_iters_ += info.gmres_iters;
   forcing_it_ = std::max(forcing_it_, info.forcing);
   corrections_ += info.corrections;

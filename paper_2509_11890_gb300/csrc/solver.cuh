@@ -50,6 +50,7 @@ struct Options {
   // finishing phase (Section 3.5): absolute tolerance (0: off) and the barrier relaxation range
   double finish_tol = 0.0, nu0 = 1e-6, nu_max = 1e-3;
   int refine_sweeps = 1;  // closing FP64 sweeps of a reduced-precision AMEn solve
+  int fp32_factors = 1;   // FP64: dense local solves may use FP32 factors refined in FP64
 };
 
 struct IterLog {
@@ -166,10 +167,20 @@ class Solver {
 };
 
 // Solves K x = b (N x N row-major FP64 on the device, kept; b becomes x) as the
-// dense local solves of the AMEn sweep do: LU with partial pivoting in FP64, or
-// one FP32 factorisation refined in FP64 for the reduced precisions. Returns
-// the FP64 relative residual; *corrections counts the refinement solves.
-double dense_local_solve(int prec, int N, double* K, double* b, int* corrections);
+// dense local solves of the AMEn sweep do. n_lz > 0: K is a reduced projected
+// system whose last n_lz rows and first n_lz columns hold the symmetric
+// positive definite LZ block, solved by block elimination (Cholesky of LZ, LU
+// of the multipliers' Schur complement) with FP64 refinement; otherwise, or
+// when LZ does not factor, LU with partial pivoting in FP64, or one FP32
+// factorisation refined in FP64 for the reduced precisions. Returns the FP64
+// relative residual; *corrections counts the refinement solves.
+double dense_local_solve(int prec, int N, double* K, double* b, int* corrections, int n_lz = 0);
+
+// Block-elimination solves completed, those of them with FP32 factors, those
+// that fell back to the LU of the whole system, and the factorisations that
+// stopped at a pivot of L_Z that was not positive, since the last reset.
+void kkt_counts(unsigned long long* block, unsigned long long* fp32, unsigned long long* fallback,
+                unsigned long long* not_pd, bool reset);
 
 // min over e of <e, dM e>/<e, M e> (M positive definite): one-site ALS and
 // two-site DMRG sweeps (relative SVD truncation tolerance tol at each split).
