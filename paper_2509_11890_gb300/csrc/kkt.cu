@@ -165,7 +165,60 @@ void solve_with(int m, const T* F, const int* piv, const int* perm, const double
   }
 }
 
+// aug = [ (M + M^T) / 2 | (D + D^T) / 2 | I ] (n x 3n)
+__global__ void build_pencil_aug_kernel(int n, const double* __restrict__ M, const double* __restrict__ D,
+                                        double* __restrict__ aug) {
+  const long long ld = 3LL * n, tot = (long long)n * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), c = (int)(e % ld);
+    double v;
+    if (c < n) v = 0.5 * (M[(long long)i * n + c] + M[(long long)c * n + i]);
+    else if (c < 2 * n) v = 0.5 * (D[(long long)i * n + c - n] + D[(long long)(c - n) * n + i]);
+    else v = (c - 2 * n == i) ? 1.0 : 0.0;
+    aug[e] = v;
+  }
+}
+
+// The bordered Cholesky of the file comment on aug (n rows, ld columns, the
+// first n of them the symmetric matrix): returns false when a pivot was not
+// positive. dvec receives the diagonal of U.
+template <typename T>
+bool bordered_cholesky(int n, int ld, T* aug, T* dvec, cudaStream_t st) {
+  DBuf<int> bad(1);
+  TT_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int), st));
+  for (int j0 = 0; j0 < n; j0 += kNb) {
+    const int jb = std::min(kNb, n - j0), r1 = j0 + jb;
+    const int blocks = std::max(1, std::min(ceil_div(ld - r1, kRowThreads), 152 * 8));
+    chol_row_kernel<T><<<blocks, kRowThreads, 0, st>>>(ld, aug, dvec, j0, jb, bad.get());
+    count_launch();
+    if (r1 < n) {
+      T* row = aug + (size_t)j0 * ld + r1;
+      gemm_rm<T>(true, false, n - r1, ld - r1, jb, T(-1), row, ld, 0, row, ld, 0, T(1), aug + (size_t)r1 * ld + r1,
+                 ld, 0, 1, st);
+    }
+  }
+  check_launch("bordered cholesky");
+  int hbad = 0;
+  TT_CUDA(cudaMemcpyAsync(&hbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(sync_stream(st));
+  return hbad == 0;
+}
+
 }  // namespace
+
+bool chol_reduce(int n, const double* M, const double* D, double* S, double* Linv, cudaStream_t st) {
+  TT_CHECK(n > 0, TT_E_INVALID_ARG, "chol_reduce: empty pencil");
+  const int ld = 3 * n;
+  DBuf<double> aug((size_t)n * ld), dvec((size_t)n);
+  build_pencil_aug_kernel<<<grid_of((long long)n * ld), 256, 0, st>>>(n, M, D, aug.get());
+  count_launch();
+  if (!bordered_cholesky<double>(n, ld, aug.get(), dvec.get(), st)) return false;
+  // W = U^-T D_s = L^-1 D_s in columns n..2n-1, L^-1 in columns 2n..3n-1
+  dev_copy2d(Linv, n, aug.get() + 2 * n, ld, n, n, 1.0, st);
+  gemm_rm<double>(false, true, n, n, n, 1.0, aug.get() + n, ld, 0, Linv, n, 0, 0.0, S, n, 0, 1, st);
+  return true;
+}
 
 template <typename T>
 bool kkt_factor(int N, int n, const double* K, KktFactors<T>& f, cudaStream_t st) {
@@ -176,26 +229,9 @@ bool kkt_factor(int N, int n, const double* K, KktFactors<T>& f, cudaStream_t st
   f.n = n;
   f.nm = nm;
   DBuf<T> aug((size_t)n * ld), dvec((size_t)n);
-  DBuf<int> bad(1);
-  TT_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int), st));
   build_aug_kernel<T><<<grid_of((long long)n * ld), 256, 0, st>>>(N, n, nm, K, aug.get(), ld);
   count_launch();
-  for (int j0 = 0; j0 < n; j0 += kNb) {
-    const int jb = std::min(kNb, n - j0), r1 = j0 + jb;
-    const int blocks = std::max(1, std::min(ceil_div(ld - r1, kRowThreads), 152 * 8));
-    chol_row_kernel<T><<<blocks, kRowThreads, 0, st>>>(ld, aug.get(), dvec.get(), j0, jb, bad.get());
-    count_launch();
-    if (r1 < n) {
-      T* row = aug.get() + (size_t)j0 * ld + r1;
-      gemm_rm<T>(true, false, n - r1, ld - r1, jb, T(-1), row, ld, 0, row, ld, 0, T(1),
-                 aug.get() + (size_t)r1 * ld + r1, ld, 0, 1, st);
-    }
-  }
-  check_launch("kkt bordered cholesky");
-  int hbad = 0;
-  TT_CUDA(cudaMemcpyAsync(&hbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
-  TT_CUDA(sync_stream(st));
-  if (hbad) return false;
+  if (!bordered_cholesky<T>(n, ld, aug.get(), dvec.get(), st)) return false;
   f.lz.alloc((size_t)n * n);
   chol_to_lu_kernel<T><<<grid_of((long long)n * n), 256, 0, st>>>(n, ld, aug.get(), dvec.get(), f.lz.get());
   count_launch();

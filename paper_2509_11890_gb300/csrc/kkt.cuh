@@ -37,6 +37,14 @@ bool kkt_factor(int N, int n, const double* K, KktFactors<T>& f, cudaStream_t st
 template <typename T>
 void kkt_apply(const KktFactors<T>& f, const double* K, const double* b, double* x, cudaStream_t st);
 
+// Reduction of the symmetric-definite pencil (D, M) of the step-length
+// eigenproblems (Section 3.4) with the same bordered Cholesky, carrying D and
+// I as right-hand sides: M_s = L L^T for the symmetric parts M_s, D_s of M,
+// D (n x n row-major FP64), S = L^-1 D_s L^-T (n x n) and Linv = L^-1 (lower
+// triangular, n x n row-major). Returns false when M_s is not numerically
+// positive definite (S and Linv then unspecified).
+bool chol_reduce(int n, const double* M, const double* D, double* S, double* Linv, cudaStream_t st);
+
 // Algorithmic flops of one factorisation and of one application.
 double kkt_factor_flops(int N, int n);
 double kkt_apply_flops(int N, int n);

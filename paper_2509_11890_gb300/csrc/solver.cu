@@ -988,30 +988,16 @@ DTT BlockTT::component(int b) const {
 static double local_min_eig(int nl, const double* Mk, const double* Dk, double* x) {
   cudaStream_t st = cur_stream();
   size_t nn = (size_t)nl * nl;
-  DBuf<double> L(nn), Ms(nn), Ds(nn), tmp(nn), S(nn);
-  // symmetrise
-  transpose<double>(nl, nl, Mk, tmp.get(), st);
-  dev_copy(Ms.get(), Mk, nn, st);
-  dev_axpy(Ms.get(), tmp.get(), nn, 1.0, st);
-  dev_scale(Ms.get(), nn, 0.5, st);
-  transpose<double>(nl, nl, Dk, tmp.get(), st);
-  dev_copy(Ds.get(), Dk, nn, st);
-  dev_axpy(Ds.get(), tmp.get(), nn, 1.0, st);
-  dev_scale(Ds.get(), nn, 0.5, st);
-  dev_copy(L.get(), Ms.get(), nn, st);
-  DBuf<int> nonpos(1);
-  TT_CUDA(cudaMemsetAsync(nonpos.get(), 0, sizeof(int), st));
-  cholesky_lower<double>(nl, L.get(), st, nonpos.get());
-  int h_nonpos = 0;
-  TT_CUDA(cudaMemcpyAsync(&h_nonpos, nonpos.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
-  TT_CUDA(sync_stream(st));
-  // Section 3.4: an iterate that is not positive definite shows in its
-  // projection; the step length is then undefined and the error is raised
-  TT_CHECK(!h_nonpos, TT_E_NOT_PD, "step length: the projected iterate is not positive definite");
-  tri_lower_inverse<double>(nl, L.get(), st);  // L <- L^{-1}
-  // S = Li Ds Li^T
-  gemm_rm<double>(false, false, nl, nl, nl, 1.0, L.get(), nl, 0, Ds.get(), nl, 0, 0.0, tmp.get(), nl, 0, 1, st);
-  gemm_rm<double>(false, true, nl, nl, nl, 1.0, tmp.get(), nl, 0, L.get(), nl, 0, 0.0, S.get(), nl, 0, 1, st);
+  DBuf<double> L(nn), tmp(nn), S(nn);
+  // Ms = L L^T and S = Li Ds Li^T (Ms, Ds the symmetric parts) by the
+  // bordered Cholesky; Section 3.4: an iterate that is not positive definite
+  // shows in its projection; the step length is then undefined and the error
+  // is raised
+  std::optional<ProfScope> ps_red;
+  ps_red.emplace("eig.reduce");
+  TT_CHECK(chol_reduce(nl, Mk, Dk, S.get(), L.get(), st), TT_E_NOT_PD,
+           "step length: the projected iterate is not positive definite");
+  ps_red.reset();
   transpose<double>(nl, nl, S.get(), tmp.get(), st);
   dev_axpy(S.get(), tmp.get(), nn, 1.0, st);
   dev_scale(S.get(), nn, 0.5, st);
@@ -1028,7 +1014,10 @@ static double local_min_eig(int nl, const double* Mk, const double* Dk, double* 
   dev_axpy(Sh.get(), dI.get(), nn, 1.0, st);
   DBuf<float> Sf(nn), U(nn), Sv(nl), Vt(nn);
   to_f32(Sh.get(), Sf.get(), nn, st);
-  svd_thin<float>(MatView<float>{Sf.get(), nl, nl, nl, 1}, U.get(), Sv.get(), Vt.get(), st, kSvdLeft);
+  {
+    ProfScope ps_svd("eig.svd");
+    svd_thin<float>(MatView<float>{Sf.get(), nl, nl, nl, 1}, U.get(), Sv.get(), Vt.get(), st, kSvdLeft);
+  }
   DBuf<double> v(nl), Sv64(nl);
   transpose<float>(nl, nl, U.get(), Vt.get(), st);  // row nl-1 of U^T = last column of U
   to_f64(Vt.get() + (size_t)(nl - 1) * nl, v.get(), nl, st);
