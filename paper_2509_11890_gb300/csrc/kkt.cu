@@ -151,16 +151,18 @@ __global__ void iota_kernel(int n, int* p) {
 
 inline int grid_of(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8)); }
 
-// out = M^-1 in for factors of type T (interchanges piv, composed in perm); FP64 vectors
+// out = M^-1 in for factors of type T (interchanges piv, composed in perm,
+// diagonal-block inverses dinv); FP64 vectors
 template <typename T>
-void solve_with(int m, const T* F, const int* piv, const int* perm, const double* in, double* out, cudaStream_t st) {
+void solve_with(int m, const T* F, const int* piv, const int* perm, const T* dinv, const double* in, double* out,
+                cudaStream_t st) {
   if constexpr (std::is_same<T, double>::value) {
     if (out != in) dev_copy(out, in, (size_t)m, st);
-    lu_solve_factored<double>(m, F, piv, out, st, perm);
+    lu_solve_factored<double>(m, F, piv, out, st, perm, dinv);
   } else {
     DBuf<float> v((size_t)m);
     to_f32(in, v.get(), (size_t)m, st);
-    lu_solve_factored<float>(m, F, piv, v.get(), st, perm);
+    lu_solve_factored<float>(m, F, piv, v.get(), st, perm, dinv);
     to_f64(v.get(), out, (size_t)m, st);
   }
 }
@@ -235,6 +237,8 @@ bool kkt_factor(int N, int n, const double* K, KktFactors<T>& f, cudaStream_t st
   f.lz.alloc((size_t)n * n);
   chol_to_lu_kernel<T><<<grid_of((long long)n * n), 256, 0, st>>>(n, ld, aug.get(), dvec.get(), f.lz.get());
   count_launch();
+  f.lz_dinv.alloc(lu_diag_inv_size(n));
+  lu_diag_inverses<T>(n, f.lz.get(), f.lz_dinv.get(), st);
   f.ident.alloc((size_t)n);
   iota_kernel<<<grid_of(n), 256, 0, st>>>(n, f.ident.get());
   count_launch();
@@ -249,6 +253,8 @@ bool kkt_factor(int N, int n, const double* K, KktFactors<T>& f, cudaStream_t st
   lu_factor<T>(nm, f.s.get(), f.ipiv.get(), st);
   f.perm.alloc((size_t)nm);
   lu_perm(nm, f.ipiv.get(), f.perm.get(), st);
+  f.s_dinv.alloc(lu_diag_inv_size(nm));
+  lu_diag_inverses<T>(nm, f.s.get(), f.s_dinv.get(), st);
   return true;
 }
 
@@ -257,15 +263,15 @@ void kkt_apply(const KktFactors<T>& f, const double* K, const double* b, double*
   const int N = f.N, n = f.n, nm = f.nm;
   DBuf<double> u((size_t)n), r((size_t)nm);
   // u = LZ^-1 b_c
-  solve_with<T>(n, f.lz.get(), f.ident.get(), f.ident.get(), b + nm, u.get(), st);
+  solve_with<T>(n, f.lz.get(), f.ident.get(), f.ident.get(), f.lz_dinv.get(), b + nm, u.get(), st);
   // dl = S^-1 (b_m - E u)
   dev_copy(r.get(), b, (size_t)nm, st);
   gemm_rm<double>(false, false, nm, 1, n, -1.0, K, N, 0, u.get(), 1, 0, 1.0, r.get(), 1, 0, 1, st);
-  solve_with<T>(nm, f.s.get(), f.ipiv.get(), f.perm.get(), r.get(), x + n, st);
+  solve_with<T>(nm, f.s.get(), f.ipiv.get(), f.perm.get(), f.s_dinv.get(), r.get(), x + n, st);
   // dX = LZ^-1 (b_c - G dl)
   dev_copy(x, b + nm, (size_t)n, st);
   gemm_rm<double>(false, false, n, 1, nm, -1.0, K + (size_t)nm * N + n, N, 0, x + n, 1, 0, 1.0, x, 1, 0, 1, st);
-  solve_with<T>(n, f.lz.get(), f.ident.get(), f.ident.get(), x, x, st);
+  solve_with<T>(n, f.lz.get(), f.ident.get(), f.ident.get(), f.lz_dinv.get(), x, x, st);
 }
 
 double kkt_factor_flops(int N, int n) {

@@ -24,6 +24,7 @@ struct KktFactors {
   DBuf<int> ipiv;  // its interchanges
   DBuf<int> perm;  // composed (lu_perm)
   DBuf<int> ident; // 0, 1, ..., n-1
+  DBuf<T> lz_dinv, s_dinv;  // diagonal-block inverses of both (lu_diag_inverses)
 };
 
 // Factors K (kept). Returns false when the symmetric part of the LZ block is

@@ -1168,57 +1168,93 @@ constexpr int kApplyNB = 64;
 constexpr int kApplyCtas = 8;
 constexpr int kApplyThreads = 512;
 
+// The inverses of the 64 x 64 diagonal blocks of a factored system in the
+// layout lu_apply_kernel reads (block b covers rows and columns b*64 ..
+// b*64+63, cut at n): dinv[b] holds the inverse of the block's lower
+// triangle (diagonal included) in its lower triangle and the strictly upper
+// part of the inverse of its unit upper triangle above the diagonal. One CTA
+// per block; thread j computes column j of the lower inverse (forward
+// substitution), thread 64 + j column j of the upper one. A zero diagonal
+// entry gives zero, as the substitution of lu_apply_kernel does.
+template <typename T>
+__global__ void __launch_bounds__(2 * kApplyNB) lu_diag_inv_kernel(int n, const T* __restrict__ B,
+                                                                   T* __restrict__ dinv) {
+  // two padded 64 x 65 tiles in dynamic shared memory (66.5 KB in FP64)
+  extern __shared__ __align__(16) unsigned char inv_smem[];
+  T(*tri)[kApplyNB + 1] = reinterpret_cast<T(*)[kApplyNB + 1]>(inv_smem);
+  T(*out)[kApplyNB + 1] = reinterpret_cast<T(*)[kApplyNB + 1]>(inv_smem + sizeof(T) * kApplyNB * (kApplyNB + 1));
+  const int b = blockIdx.x, i0 = b * kApplyNB, ib = n - i0 < kApplyNB ? n - i0 : kApplyNB;
+  for (int e = threadIdx.x; e < kApplyNB * kApplyNB; e += blockDim.x) {
+    const int r = e / kApplyNB, c = e % kApplyNB;
+    tri[r][c] = (r < ib && c < ib) ? B[(long long)(i0 + r) * n + i0 + c] : T(0);
+    out[r][c] = T(0);
+  }
+  __syncthreads();
+  const int j = threadIdx.x % kApplyNB;
+  if (j < ib) {
+    if (threadIdx.x < kApplyNB) {
+      // lower with diagonal: x_r = (delta_rj - sum_{j <= t < r} T[r][t] x_t) / T[r][r]
+      out[j][j] = tri[j][j] != T(0) ? T(1) / tri[j][j] : T(0);
+      for (int r = j + 1; r < ib; ++r) {
+        T sum = T(0);
+        for (int t = j; t < r; ++t) sum += tri[r][t] * out[t][j];
+        out[r][j] = tri[r][r] != T(0) ? -sum / tri[r][r] : T(0);
+      }
+    } else {
+      // unit upper: x_j = 1, x_r = -sum_{r < t <= j} U[r][t] x_t for r < j;
+      // the unit diagonal stays implicit (out[j][j] belongs to the lower inverse)
+      for (int r = j - 1; r >= 0; --r) {
+        T sum = tri[r][j];
+        for (int t = r + 1; t < j; ++t) sum += tri[r][t] * out[t][j];
+        out[r][j] = -sum;
+      }
+    }
+  }
+  __syncthreads();
+  T* D = dinv + (size_t)b * kApplyNB * kApplyNB;
+  for (int e = threadIdx.x; e < kApplyNB * kApplyNB; e += blockDim.x) D[e] = out[e / kApplyNB][e % kApplyNB];
+}
+
 // The solves of lu_apply_kernel spread over a cluster of kApplyCtas CTAs:
-// U^T y = b by 64-row steps from the top, then L^T z = y from the bottom,
-// then x[i] = z[perm[i]] (perm null: x = z). In each step every CTA loads
-// the step's 64 x 64 diagonal triangle into shared memory and solves it in
-// one warp (two unknowns per lane) from the step's right-hand side, which the
-// previous steps have completed; CTA 0 stores the step's unknowns, and every
-// warp of the cluster subtracts their contribution from the rows it owns
-// below (forward) or above (backward) the step, one row per warp at a time
-// with the 64 products in its lanes. One cluster barrier (hardware, with
-// release / acquire ordering of the CTAs' global writes) ends each step, so
-// no step reads a right-hand side entry another CTA is still updating.
-// b is the right-hand side on entry (updated in place by the forward steps)
-// and x on exit; y and w are n-entry scratch vectors. Entries that another
-// CTA wrote are read and written at L2 (ld/st.cg), past the SM's L1.
+// U^T y = b by 64-row blocks from the top, then L^T z = y from the bottom,
+// then x[i] = z[perm[i]] (perm null: x = z). In each step every CTA takes
+// the block's right-hand side, which the previous steps have completed, and
+// multiplies it by the block's precomputed triangle inverse (dinv, from
+// lu_diag_inv_kernel; one row per warp), so no step runs a serial chain;
+// CTA 0 stores the block's unknowns, and every warp of the cluster subtracts
+// their contribution from the rows it owns below (forward) or above
+// (backward) the block, one row per warp at a time with the 64 products in
+// its lanes. One cluster barrier (hardware, with release / acquire ordering
+// of the CTAs' global writes) ends each step, so no step reads a right-hand
+// side entry another CTA is still updating. b is the right-hand side on
+// entry (updated in place by the forward steps) and x on exit; y and w are
+// n-entry scratch vectors. Entries that another CTA wrote are read and
+// written at L2 (ld/st.cg), past the SM's L1.
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads) lu_apply_cluster_kernel(int n, const T* __restrict__ B,
+                                                                         const T* __restrict__ dinv,
                                                                          const int* __restrict__ perm, T* b, T* y,
                                                                          T* w) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  __shared__ T tri[kApplyNB][kApplyNB + 1];
+  __shared__ T rhs[kApplyNB];
   __shared__ T xb[kApplyNB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int kWarpsPerCta = kApplyThreads / 32;
   const int gwarp = rank * kWarpsPerCta + warp, nwarps = kApplyCtas * kWarpsPerCta;
+  const int nblk = (n + kApplyNB - 1) / kApplyNB;
   // forward: U^T y = b (lower triangle of the buffer, diagonal included)
-  for (int i0 = 0; i0 < n; i0 += kApplyNB) {
-    const int ib = n - i0 < kApplyNB ? n - i0 : kApplyNB, i1 = i0 + ib;
-    for (int e = tid; e < ib * ib; e += kApplyThreads) {
-      const int r = e / ib, c = e % ib;
-      if (c <= r) tri[r][c] = B[(long long)(i0 + r) * n + i0 + c];
-    }
-    if (tid < ib) xb[tid] = __ldcg(b + i0 + tid);
+  for (int blk = 0; blk < nblk; ++blk) {
+    const int i0 = blk * kApplyNB, ib = n - i0 < kApplyNB ? n - i0 : kApplyNB, i1 = i0 + ib;
+    const T* D = dinv + (size_t)blk * kApplyNB * kApplyNB;
+    if (tid < ib) rhs[tid] = __ldcg(b + i0 + tid);
     __syncthreads();
-    if (warp == 0) {
-      T v0 = lane < ib ? xb[lane] : T(0), v1 = lane + 32 < ib ? xb[lane + 32] : T(0);
-      for (int t = 0; t < ib; ++t) {
-        T xt;
-        if (t < 32) {
-          if (lane == t) v0 = tri[t][t] != T(0) ? v0 / tri[t][t] : T(0);
-          xt = __shfl_sync(0xffffffffu, v0, t);
-        } else {
-          if (lane == t - 32) v1 = tri[t][t] != T(0) ? v1 / tri[t][t] : T(0);
-          xt = __shfl_sync(0xffffffffu, v1, t - 32);
-        }
-        if (lane > t && lane < ib) v0 -= tri[lane][t] * xt;
-        if (lane + 32 > t && lane + 32 < ib) v1 -= tri[lane + 32][t] * xt;
-      }
-      if (lane < ib) xb[lane] = v0;
-      if (lane + 32 < ib) xb[lane + 32] = v1;
+    for (int r = warp; r < ib; r += kWarpsPerCta) {
+      const T* Dr = D + (size_t)r * kApplyNB;
+      T s = (lane <= r ? Dr[lane] * rhs[lane] : T(0)) + (lane + 32 <= r ? Dr[lane + 32] * rhs[lane + 32] : T(0));
+      s = warp_sum(s);
+      if (lane == 0) xb[r] = s;
     }
     __syncthreads();
     if (rank == 0 && tid < ib) __stcg(y + i0 + tid, xb[tid]);
@@ -1231,23 +1267,17 @@ __global__ void __launch_bounds__(kApplyThreads) lu_apply_cluster_kernel(int n, 
     cluster.sync();
   }
   // backward: L^T z = y (strict upper triangle of the buffer, unit diagonal)
-  for (int i1 = n; i1 > 0;) {
-    const int i0 = i1 - kApplyNB > 0 ? i1 - kApplyNB : 0, ib = i1 - i0;
-    for (int e = tid; e < ib * ib; e += kApplyThreads) {
-      const int r = e / ib, c = e % ib;
-      if (c > r) tri[r][c] = B[(long long)(i0 + r) * n + i0 + c];
-    }
-    if (tid < ib) xb[tid] = __ldcg(y + i0 + tid);
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int i0 = blk * kApplyNB, ib = n - i0 < kApplyNB ? n - i0 : kApplyNB;
+    const T* D = dinv + (size_t)blk * kApplyNB * kApplyNB;
+    if (tid < ib) rhs[tid] = __ldcg(y + i0 + tid);
     __syncthreads();
-    if (warp == 0) {
-      T v0 = lane < ib ? xb[lane] : T(0), v1 = lane + 32 < ib ? xb[lane + 32] : T(0);
-      for (int t = ib - 1; t > 0; --t) {
-        const T xt = t < 32 ? __shfl_sync(0xffffffffu, v0, t) : __shfl_sync(0xffffffffu, v1, t - 32);
-        if (lane < t) v0 -= tri[lane][t] * xt;
-        if (lane + 32 < t) v1 -= tri[lane + 32][t] * xt;
-      }
-      if (lane < ib) xb[lane] = v0;
-      if (lane + 32 < ib) xb[lane + 32] = v1;
+    for (int r = warp; r < ib; r += kWarpsPerCta) {
+      const T* Dr = D + (size_t)r * kApplyNB;
+      T s = (lane > r && lane < ib ? Dr[lane] * rhs[lane] : T(0)) +
+            (lane + 32 > r && lane + 32 < ib ? Dr[lane + 32] * rhs[lane + 32] : T(0));
+      s = warp_sum(s);
+      if (lane == 0) xb[r] = rhs[r] + s;
     }
     __syncthreads();
     if (rank == 0 && tid < ib) __stcg(w + i0 + tid, xb[tid]);
@@ -1258,7 +1288,6 @@ __global__ void __launch_bounds__(kApplyThreads) lu_apply_cluster_kernel(int n, 
       if (lane == 0) __stcg(y + row, __ldcg(y + row) - s);
     }
     cluster.sync();
-    i1 = i0;
   }
   // x = P^T z as a gather
   for (int i = rank * kApplyThreads + tid; i < n; i += kApplyCtas * kApplyThreads)
@@ -1306,14 +1335,36 @@ void lu_perm(int n, const int* ipiv, int* perm, cudaStream_t st) {
   check_launch("lu_perm");
 }
 
+size_t lu_diag_inv_size(int n) { return (size_t)((n + kApplyNB - 1) / kApplyNB) * kApplyNB * kApplyNB; }
+
+template <typename T>
+void lu_diag_inverses(int n, const T* LU, T* dinv, cudaStream_t st) {
+  if (n <= 0) return;
+  constexpr size_t smem = 2 * sizeof(T) * kApplyNB * (kApplyNB + 1);
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(lu_diag_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  TT_CUDA(attr_err);
+  lu_diag_inv_kernel<T><<<(n + kApplyNB - 1) / kApplyNB, 2 * kApplyNB, smem, st>>>(n, LU, dinv);
+  count_launch();
+  check_launch("lu_diag_inv_kernel");
+}
+
 namespace {
 
 // Systems from this size on are solved by the cluster kernel.
 constexpr int kApplyClusterMin = 160;
 
 template <typename T>
-void lu_apply_cluster(int n, const T* LU, const int* perm, T* b, cudaStream_t st) {
-  DBuf<T> y((size_t)n), w((size_t)n);
+void lu_apply_cluster(int n, const T* LU, const int* perm, const T* dinv, T* b, cudaStream_t st) {
+  DBuf<T> y((size_t)n), w((size_t)n), dtmp;
+  if (!dinv) {
+    dtmp.alloc(lu_diag_inv_size(n));
+    lu_diag_inverses<T>(n, LU, dtmp.get(), st);
+    dinv = dtmp.get();
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kApplyCtas, 1, 1);
   cfg.blockDim = dim3(kApplyThreads, 1, 1);
@@ -1326,7 +1377,7 @@ void lu_apply_cluster(int n, const T* LU, const int* perm, T* b, cudaStream_t st
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  TT_CUDA(cudaLaunchKernelEx(&cfg, lu_apply_cluster_kernel<T>, n, LU, perm, b, y.get(), w.get()));
+  TT_CUDA(cudaLaunchKernelEx(&cfg, lu_apply_cluster_kernel<T>, n, LU, dinv, perm, b, y.get(), w.get()));
   count_launch();
   check_launch("lu_apply_cluster_kernel");
 }
@@ -1334,15 +1385,15 @@ void lu_apply_cluster(int n, const T* LU, const int* perm, T* b, cudaStream_t st
 }  // namespace
 
 template <typename T>
-void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st, const int* perm) {
+void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st, const int* perm, const T* dinv) {
   if (n <= 0) return;
   if (n >= kApplyClusterMin) {
     if (perm) {
-      lu_apply_cluster<T>(n, LU, perm, b, st);
+      lu_apply_cluster<T>(n, LU, perm, dinv, b, st);
     } else {
       DBuf<int> p((size_t)n);
       lu_perm(n, ipiv, p.get(), st);
-      lu_apply_cluster<T>(n, LU, p.get(), b, st);
+      lu_apply_cluster<T>(n, LU, p.get(), dinv, b, st);
     }
     return;
   }
@@ -1401,7 +1452,8 @@ void transpose(int m, int n, const T* in, T* out, cudaStream_t st) {
   template void svd_thin<T>(MatView<T>, T*, T*, T*, cudaStream_t, SvdSide);     \
   template void lu_solve<T>(int, T*, T*, cudaStream_t);                         \
   template void lu_factor<T>(int, T*, int*, cudaStream_t);                      \
-  template void lu_solve_factored<T>(int, const T*, const int*, T*, cudaStream_t, const int*); \
+  template void lu_solve_factored<T>(int, const T*, const int*, T*, cudaStream_t, const int*, const T*); \
+  template void lu_diag_inverses<T>(int, const T*, T*, cudaStream_t);           \
   template void cholesky_lower<T>(int, T*, cudaStream_t, int*);                 \
   template void tri_lower_inverse<T>(int, T*, cudaStream_t);                    \
   template void transpose<T>(int, int, const T*, T*, cudaStream_t);

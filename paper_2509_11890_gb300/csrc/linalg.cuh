@@ -48,7 +48,14 @@ void lu_solve(int n, T* A, T* b, cudaStream_t st);
 template <typename T>
 void lu_factor(int n, T* A, int* ipiv, cudaStream_t st);
 template <typename T>
-void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st, const int* perm = nullptr);
+void lu_solve_factored(int n, const T* LU, const int* ipiv, T* b, cudaStream_t st, const int* perm = nullptr,
+                       const T* dinv = nullptr);
+// The inverses of the 64 x 64 diagonal blocks of the factors that the
+// cluster solves of lu_solve_factored use (dinv: lu_diag_inv_size(n)
+// entries); computed once per factorisation they save one launch per solve.
+size_t lu_diag_inv_size(int n);
+template <typename T>
+void lu_diag_inverses(int n, const T* LU, T* dinv, cudaStream_t st);
 // perm[i] = the row of the solution of the permuted system that lands at
 // position i: the interchanges ipiv of lu_factor composed (n <= 25600).
 void lu_perm(int n, const int* ipiv, int* perm, cudaStream_t st);

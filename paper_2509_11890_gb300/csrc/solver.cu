@@ -312,11 +312,13 @@ void lu_refined_f32(int N, const double* K, const double* b, double* x, double* 
   to_f32(K, kf.get(), nn, st);
   lu_factor<float>(N, kf.get(), ipiv.get(), st);
   lu_perm(N, ipiv.get(), perm.get(), st);
+  DBuf<float> dinv(lu_diag_inv_size(N));
+  lu_diag_inverses<float>(N, kf.get(), dinv.get(), st);
   *flops += 2.0 / 3.0 * (double)N * N * N;
   double prev = 1.0;
   for (int it = 0; it < max_solves; ++it) {
     to_f32(r, rf.get(), N, st);
-    lu_solve_factored<float>(N, kf.get(), ipiv.get(), rf.get(), st, perm.get());
+    lu_solve_factored<float>(N, kf.get(), ipiv.get(), rf.get(), st, perm.get(), dinv.get());
     *flops += 2.0 * (double)N * N;
     to_f64(rf.get(), dx.get(), N, st);
     dev_axpy(x, dx.get(), N, 1.0, st);
