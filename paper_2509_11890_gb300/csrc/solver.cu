@@ -1360,11 +1360,11 @@ Problem build_cc(const DTT& cp, const DTT& cm, const DTT& a) {
 // ---------------------------------------------------------------------------
 // The step-length eigensolver the options select: two-site DMRG (Section 3.4)
 // or one-site ALS, FP64 throughout.
-static double gen_eig(const Options& o, const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& rnd, int rank,
+// The eigensolver's random starts and kicks come from a sub-stream of the
+// main stream (forked by the caller), so how many sweeps it runs does not
+// move the main stream.
+static double gen_eig(const Options& o, const DTT& M, const DTT& dM, DTT* e, bool warm, Counter& sub, int rank,
                       int sweeps) {
-  // the eigensolver's random starts and kicks come from a sub-stream, so how
-  // many sweeps it runs does not move the main stream
-  Counter sub = rnd.fork();
   if (o.eig_two_site) return min_gen_eig_dmrg(M, dM, e, warm, sub, rank, sweeps, TT_FP64, kDmrgTol, kEigStall);
   return min_gen_eig(M, dM, e, warm, sub, rank, sweeps, TT_FP64);
 }
@@ -1394,7 +1394,8 @@ Solver::Solver(Problem p, const Options& o) : p_(std::move(p)), o_(o) {
   Y_ = tt_zeros_like_modes(d, 2, 2);
   if (p_.ineq) {
     DTT e;
-    double lmin = gen_eig(o_, I_, p_.ones_t, &e, false, rnd_, 2, 6);
+    Counter sub = rnd_.fork();
+    double lmin = gen_eig(o_, I_, p_.ones_t, &e, false, sub, 2, 6);
     double alpha_p = lmin < 0 ? p_.lam0 * step_from_lambda(lmin) : p_.lam0;
     X_ = tt_add(tt_scale(I_, p_.lam0), p_.ones_t, 1.0, alpha_p / 10.0);
     T_ = tt_scale(p_.ones_t, p_.lam0_ineq);
@@ -1523,35 +1524,91 @@ void Solver::direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, c
   }
 }
 
-double Solver::max_step(const DTT& M0, const DTT& dM, DTT* e) {
+double Solver::max_step(const DTT& M0, const DTT& dM, DTT* e, Counter* sub) {
   bool warm = (e == &eX_) ? haveX_ : haveZ_;
   // finishing phase: the relaxed cone M + nu I >= 0 (Section 3.5)
   const DTT M = nu_ > 0.0 ? tt_add(M0, I_, 1.0, nu_) : M0;
-  double lam = gen_eig(o_, M, tt_sym(dM), e, warm, rnd_, o_.eig_rank, o_.eig_sweeps);
+  Counter own;
+  if (!sub) {
+    own = rnd_.fork();
+    sub = &own;
+  }
+  double lam = gen_eig(o_, M, tt_sym(dM), e, warm, *sub, o_.eig_rank, o_.eig_sweeps);
   if (e == &eX_) haveX_ = true; else haveZ_ = true;
   return step_from_lambda(lam);
 }
 
-double Solver::max_step_diag(const DTT& v, const DTT& dv, DTT* e) {
+double Solver::max_step_diag(const DTT& v, const DTT& dv, DTT* e, Counter* sub) {
   DTT idle = tt_add(vecv(tt_ones_mat(p_.d, 2)), vecv(p_.ones_t), 1.0, -1.0);
   DTT M = tt_diag(tt_add(v, idle, 1.0, 1.0));
   if (nu_ > 0.0) M = tt_add(M, tt_diag(vecv(p_.ones_t)), 1.0, nu_);
   bool warm = (e == &eS_) ? haveS_ : haveT_;
-  double lam = gen_eig(o_, M, tt_diag(dv), e, warm, rnd_, 1, o_.eig_sweeps);
+  Counter own;
+  if (!sub) {
+    own = rnd_.fork();
+    sub = &own;
+  }
+  double lam = gen_eig(o_, M, tt_diag(dv), e, warm, *sub, 1, o_.eig_sweeps);
   if (e == &eS_) haveS_ = true; else haveT_ = true;
   return step_from_lambda(lam);
 }
 
 void Solver::steps(const DTT& dX, const DTT& dT, const DTT& dZ, double* ap, double* ad) {
-  double a_p = max_step(X_, dX, &eX_);
-  double a_d = max_step(Z_, dZ, &eZ_);
+  // The step-length eigensolves of X, Z (and of the slack and T) are
+  // independent and run concurrently. Each takes the sub-stream of the main
+  // random stream that the order X, Z, s, T gives it, and a failure is
+  // reported as that order would report it: the first failing solve's
+  // error, with the main stream and the warm starts of the solves after it
+  // as if they had not run.
+  DTT ds, s;
   if (p_.ineq) {
-    DTT ds = tt_matvec(p_.A_ineq, vecv(dX));
-    DTT s = slack(X_);
-    double a_s = max_step_diag(s, ds, &eS_);
-    double a_t = max_step_diag(vecv(T_), vecv(dT), &eT_);
-    a_p = std::min(a_p, a_s);
-    a_d = std::min(a_d, a_t);
+    ds = tt_matvec(p_.A_ineq, vecv(dX));
+    s = slack(X_);
+  }
+  const int nj = p_.ineq ? 4 : 2;
+  Counter sub[4], after[4];
+  DTT* warm_e[4] = {&eX_, &eZ_, &eS_, &eT_};
+  bool* warm_f[4] = {&haveX_, &haveZ_, &haveS_, &haveT_};
+  DTT e_before[4];
+  bool f_before[4];
+  for (int j = 0; j < nj; ++j) {
+    sub[j] = rnd_.fork();
+    after[j] = rnd_;
+    e_before[j] = *warm_e[j];
+    f_before[j] = *warm_f[j];
+  }
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  std::exception_ptr err[4];
+  std::vector<std::function<void()>> jobs;
+  auto guarded_job = [&](int j, std::function<double()> f) {
+    jobs.push_back([&, j, f]() {
+      try {
+        a[j] = f();
+      } catch (...) {
+        err[j] = std::current_exception();
+      }
+    });
+  };
+  guarded_job(0, [&]() { return max_step(X_, dX, &eX_, &sub[0]); });
+  guarded_job(1, [&]() { return max_step(Z_, dZ, &eZ_, &sub[1]); });
+  if (p_.ineq) {
+    guarded_job(2, [&]() { return max_step_diag(s, ds, &eS_, &sub[2]); });
+    guarded_job(3, [&]() { return max_step_diag(vecv(T_), vecv(dT), &eT_, &sub[3]); });
+  }
+  run_concurrently(jobs, side_);
+  for (int j = 0; j < nj; ++j) {
+    if (!err[j]) continue;
+    for (int k = j + 1; k < nj; ++k) {
+      *warm_e[k] = e_before[k];
+      *warm_f[k] = f_before[k];
+    }
+    rnd_ = after[j];
+    std::rethrow_exception(err[j]);
+  }
+  double a_p = a[0], a_d = a[1];
+  if (p_.ineq) {
+    a_p = std::min(a_p, a[2]);
+    a_d = std::min(a_d, a[3]);
   }
   *ap = std::min(1.0, o_.damping * a_p);
   *ad = std::min(1.0, o_.damping * a_d);

@@ -110,8 +110,9 @@ class Solver {
   void direction(int dir, double sigma_mu, const DTT* cx, const DTT* cz, const DTT* ct, const DTT* cs,
                  bool zero_p, bool zero_d, DTT& dX, DTT& dY, DTT& dT, DTT& dZ, int* sweeps);
   void steps(const DTT& dX, const DTT& dT, const DTT& dZ, double* ap, double* ad);
-  double max_step(const DTT& M, const DTT& dM, DTT* e);
-  double max_step_diag(const DTT& v, const DTT& dv, DTT* e);
+  // sub: the random sub-stream of the eigensolve (null: forked from the main stream here)
+  double max_step(const DTT& M, const DTT& dM, DTT* e, Counter* sub = nullptr);
+  double max_step_diag(const DTT& v, const DTT& dv, DTT* e, Counter* sub = nullptr);
   DTT round_psd(const DTT& M, double delta, const DTT* shift, int var_id);
   IterLog iterate_once();
   // one iteration of the finishing phase (Section 3.5); fills log
