@@ -86,6 +86,81 @@ void run_concurrently(std::vector<std::function<void()>>& jobs, std::vector<cuda
     if (e) std::rethrow_exception(e);
 }
 
+// Side streams shared by fan_out calls (any thread), handed out and back
+// under a lock.
+struct StreamPool {
+  std::mutex mu;
+  std::vector<cudaStream_t> free;
+  std::vector<cudaStream_t> take(int n) {
+    std::lock_guard<std::mutex> lk(mu);
+    std::vector<cudaStream_t> out;
+    while ((int)out.size() < n) {
+      if (!free.empty()) {
+        out.push_back(free.back());
+        free.pop_back();
+      } else {
+        cudaStream_t s = nullptr;
+        TT_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        out.push_back(s);
+      }
+    }
+    return out;
+  }
+  void give(const std::vector<cudaStream_t>& v) {
+    std::lock_guard<std::mutex> lk(mu);
+    free.insert(free.end(), v.begin(), v.end());
+  }
+};
+StreamPool& stream_pool() {
+  static StreamPool p;
+  return p;
+}
+
+constexpr int kFanWidth = 4;
+
+// Enqueues independent jobs on up to kFanWidth side streams from the calling
+// thread: job j's launches go to side stream j mod kFanWidth, which first
+// waits for everything already queued on the calling stream, and the calling
+// stream then waits for every side stream. For jobs that only enqueue work
+// (no host synchronisation), their small kernels overlap without host
+// threads. Buffers a job allocates are stream-ordered on its side stream and
+// are safe to use and free on the calling stream afterwards; with a caller
+// allocator in scope (whose frees need not be stream-ordered) the jobs run
+// in order on the calling stream instead.
+void fan_out(const std::vector<std::function<void()>>& jobs) {
+  if (jobs.size() <= 1 || AllocScope::current()) {
+    for (auto& j : jobs) j();
+    return;
+  }
+  cudaStream_t main = cur_stream();
+  const int width = std::min<int>(kFanWidth, (int)jobs.size());
+  std::vector<cudaStream_t> side = stream_pool().take(width);
+  cudaEvent_t start = nullptr;
+  TT_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  TT_CUDA(cudaEventRecord(start, main));
+  for (cudaStream_t s : side) TT_CUDA(cudaStreamWaitEvent(s, start, 0));
+  std::exception_ptr err;
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    StreamScope::current() = side[j % width];
+    try {
+      jobs[j]();
+    } catch (...) {
+      if (!err) err = std::current_exception();
+    }
+  }
+  StreamScope::current() = main;
+  for (cudaStream_t s : side) {
+    cudaEvent_t done = nullptr;
+    TT_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    TT_CUDA(cudaEventRecord(done, s));
+    TT_CUDA(cudaStreamWaitEvent(main, done, 0));
+    TT_CUDA(cudaEventDestroy(done));
+  }
+  TT_CUDA(cudaEventDestroy(start));
+  stream_pool().give(side);
+  if (err) std::rethrow_exception(err);
+}
+
 // ---------------------------------------------------------------------------
 // environments of <W, Op V>
 // ---------------------------------------------------------------------------
@@ -584,15 +659,21 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
     for (auto& o : nd.DK) eDK.emplace_back(o, nullptr, d);
     for (auto& t : nd.rt) rt.emplace_back(t.coef, Env(t.op, &t.vec, d));
   }
+  // every environment's update as one job; the jobs are independent and go
+  // out over side streams (fan_out)
   auto for_all = [&](auto fn) {
+    std::vector<std::function<void()>> jobs;
     for (auto* v : {&eA, &eAT, &eK, &eLZ, &eLX, &eTA, &eAiT, &eDK})
-      for (Env& e : *v) fn(e);
+      for (Env& e : *v) jobs.push_back([&fn, &e]() { fn(e); });
     for (auto* v : {&rp, &rdd, &rc, &rt})
-      for (auto& pe : *v) fn(pe.second);
+      for (auto& pe : *v) jobs.push_back([&fn, &pe]() { fn(pe.second); });
+    fan_out(jobs);
   };
   {
     ProfScope ps("amen.env_init");
-    for (int k = d - 1; k >= 1; --k) for_all([&](Env& e) { e.push_right(frame, k, prec); });
+    for_all([&](Env& e) {
+      for (int k = d - 1; k >= 1; --k) e.push_right(frame, k, prec);
+    });
   }
 
   std::vector<int> blockshape = {frame.r[0], 4, frame.r[1]};
@@ -690,15 +771,15 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
       DBuf<double> A(n * n), AT(n * n), Ky(n * n), LZ(n * n), LX(n * n);
       std::optional<ProfScope> ps_part;
       ps_part.emplace("dense.local_mats");
-      eA[0].local_mat(frame, k, A.get(), prec);
-      eAT[0].local_mat(frame, k, AT.get(), prec);
-      eK[0].local_mat(frame, k, Ky.get(), prec);
-      sum_local_mats(eLZ, frame, k, LZ.get(), n, prec);
-      sum_local_mats(eLX, frame, k, LX.get(), n, prec);
       DBuf<double> r_p(n), r_d(n), r_c(n);
-      sum_local_rhs(rp, frame, k, r_p.get(), n, prec);
-      sum_local_rhs(rdd, frame, k, r_d.get(), n, prec);
-      sum_local_rhs(rc, frame, k, r_c.get(), n, prec);
+      fan_out({[&]() { eA[0].local_mat(frame, k, A.get(), prec); },
+               [&]() { eAT[0].local_mat(frame, k, AT.get(), prec); },
+               [&]() { eK[0].local_mat(frame, k, Ky.get(), prec); },
+               [&]() { sum_local_mats(eLZ, frame, k, LZ.get(), n, prec); },
+               [&]() { sum_local_mats(eLX, frame, k, LX.get(), n, prec); },
+               [&]() { sum_local_rhs(rp, frame, k, r_p.get(), n, prec); },
+               [&]() { sum_local_rhs(rdd, frame, k, r_d.get(), n, prec); },
+               [&]() { sum_local_rhs(rc, frame, k, r_c.get(), n, prec); }});
       ps_part.reset();
       ps_part.emplace("dense.assemble");
       DBuf<double> K(N * N), b(N);
