@@ -20,6 +20,11 @@
 
 namespace ttsdp {
 
+double& SvdNoiseFloor::slot() {
+  static thread_local double v = 0.0;
+  return v;
+}
+
 namespace {
 
 constexpr int kThreads = 512;
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) qr_kernel(MatView<T> A, T* W, T* tau
 template <typename T>
 __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transposed, T* Wg, T* Vg, bool w_smem,
                                                        bool v_smem, T* U, T* S, T* Vt, int* perm, const T* V0,
-                                                       bool need_v) {
+                                                       bool need_v, double rel_floor2) {
   __shared__ int s_rot;
   // the working columns live in shared memory when they fit (every rotation
   // then costs shared-memory latency instead of an L2 round trip)
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
   // columns whose squared norm is below (eps ||A||_F)^2 are numerical noise:
   // rotating against them cannot change any singular value above that level
   // and would keep the sweep from terminating on rank-deficient inputs
-  __shared__ T s_floor;
+  __shared__ T s_floor, s_floor_hi;
   {
     __shared__ T red[kWarps];
     T loc = T(0);
@@ -191,11 +196,16 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
     T fro2 = block_sum(loc, red);
     // rotating a large column against a tiny one leaves rounding noise of
     // size ~eps |large| in the tiny one, so the floor sits at the noise level
-    // of the whole matrix, (sqrt(m) eps ||A||_F)^2
-    if (tid == 0) s_floor = T(m) * eps_of<T>() * eps_of<T>() * fro2;
+    // of the whole matrix, (sqrt(m) eps ||A||_F)^2; pairs whose columns are
+    // both below rel_floor2 ||A||_F^2 (a caller that truncates far above it)
+    // are left as they are
+    if (tid == 0) {
+      s_floor = T(m) * eps_of<T>() * eps_of<T>() * fro2;
+      s_floor_hi = (T)rel_floor2 * fro2;
+    }
     __syncthreads();
   }
-  const T floor2 = s_floor;
+  const T floor2 = s_floor, floor_hi = s_floor_hi;
   const int nn = n + (n & 1);
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) s_rot = 0;
@@ -218,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) svd_kernel(MatView<T> A, bool transp
         a = warp_sum(a);
         b = warp_sum(b);
         g = warp_sum(g);
-        if (g != T(0) && a > floor2 && b > floor2 && fabs(g) > tol * sqrt(a * b)) {
+        if (g != T(0) && a > floor2 && b > floor2 && (a > floor_hi || b > floor_hi) && fabs(g) > tol * sqrt(a * b)) {
           T zeta = (b - a) / (T(2) * g);
           T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           T c = T(1) / sqrt(T(1) + t * t);
@@ -961,7 +971,7 @@ bool first_order_finish(DBuf<double>& W, DBuf<double>& V, int m, int n, bool tra
     TT_CUDA(sync_stream(st));
     for (double v : h) fro2 += v * v;
   }
-  const double floor2 = (double)m * DBL_EPSILON * DBL_EPSILON * fro2;
+  const double floor2 = std::max((double)m * DBL_EPSILON * DBL_EPSILON, SvdNoiseFloor::current()) * fro2;
   bool converged = false;
   for (int step = 0; step < 3; ++step) {
     gemm_rm<double>(true, false, n, n, m, 1.0, W.get(), n, 0, W.get(), n, 0, 0.0, G.get(), n, 0, 1, st);
@@ -1074,13 +1084,13 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st, SvdSide side) {
       MatView<double> wv{W.get(), m, n, n, 1};
       if (!tr) {
         svd_kernel<double><<<1, kThreads, smem, st>>>(wv, false, Wc.get(), Vc.get(), w_smem, v_smem, U, S, Vt,
-                                                      perm.get(), V0.get(), need_v);
+                                                      perm.get(), V0.get(), need_v, SvdNoiseFloor::current());
         count_launch();
       } else {
         // B = A^T = U_B S Vt_B  =>  A = Vt_B^T S U_B^T
         DBuf<double> UB((size_t)m * n), VtB(need_v ? (size_t)n * n : 0);
         svd_kernel<double><<<1, kThreads, smem, st>>>(wv, false, Wc.get(), Vc.get(), w_smem, v_smem, UB.get(), S,
-                                                      VtB.get(), perm.get(), V0.get(), need_v);
+                                                      VtB.get(), perm.get(), V0.get(), need_v, SvdNoiseFloor::current());
         count_launch();
         if (need_v) transpose<double>(n, n, VtB.get(), U, st);
         transpose<double>(m, n, UB.get(), Vt, st);
@@ -1090,7 +1100,7 @@ void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st, SvdSide side) {
     }
   }
   svd_kernel<T><<<1, kThreads, smem, st>>>(A, tr, Wc.get(), Vc.get(), w_smem, v_smem, U, S, Vt, perm.get(),
-                                           nullptr, need_v);
+                                           nullptr, need_v, SvdNoiseFloor::current());
   count_launch();
   check_launch("svd_kernel");
 }

@@ -31,6 +31,24 @@ enum SvdSide { kSvdBoth = 0, kSvdLeft = 1, kSvdRight = 2 };
 template <typename T>
 void svd_thin(MatView<T> A, T* U, T* S, T* Vt, cudaStream_t st, SvdSide side = kSvdBoth);
 
+// While one is in scope on this thread, svd_thin treats a pair of columns
+// whose squared norms are both below rel2 * ||A||_F^2 as converged (the
+// default floor is the rounding noise, m eps^2 ||A||_F^2). A caller that
+// truncates the spectrum at a relative level far above sqrt(rel2) keeps the
+// subspace it keeps exact and gives up only the order of directions it drops
+// anyway; the Jacobi sweeps then stop on clusters of such values.
+struct SvdNoiseFloor {
+  explicit SvdNoiseFloor(double rel2) : prev_(slot()) { slot() = rel2; }
+  ~SvdNoiseFloor() { slot() = prev_; }
+  SvdNoiseFloor(const SvdNoiseFloor&) = delete;
+  SvdNoiseFloor& operator=(const SvdNoiseFloor&) = delete;
+  static double current() { return slot(); }
+
+ private:
+  static double& slot();
+  double prev_;
+};
+
 // Solves A x = b in place (A n x n row-major, destroyed; b n-vector becomes x)
 // by LU with partial pivoting, right-looking and blocked (panel width 32).
 template <typename T>

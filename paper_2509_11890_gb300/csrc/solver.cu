@@ -860,8 +860,14 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         // reduced precision even in the FP64 refinement sweep
         std::optional<ProfScope> ps_svd;
         ps_svd.emplace("move.svd");
-        svd_prec(prec_in, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
-                 kSvdLeft);
+        {
+          // the move keeps the spectrum above move_tol / sqrt(d): directions
+          // 1000 times below it need not be resolved
+          const double fl = 1e-3 * move_tol(tol, prec) / std::sqrt((double)d);
+          SvdNoiseFloor nf(fl * fl);
+          svd_prec(prec_in, MatView<double>{mat.get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
+                   kSvdLeft);
+        }
         std::vector<double> hs = host_copy(S.get(), kk);
         ps_svd.reset();
         int keep = truncation_rank_rel(hs, move_tol(tol, prec) / std::sqrt((double)d), cap);
@@ -909,8 +915,12 @@ BlockTT amen_solve(NewtonData& nd, int d, const BlockTT* w0, double tol, int cap
         DBuf<double> U((size_t)rows * kk), S(kk), Vt((size_t)kk * cols);
         std::optional<ProfScope> ps_svd;
         ps_svd.emplace("move.svd");
-        svd_prec(prec_in, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
-                 kSvdRight);
+        {
+          const double fl = 1e-3 * move_tol(tol, prec) / std::sqrt((double)d);
+          SvdNoiseFloor nf(fl * fl);
+          svd_prec(prec_in, MatView<double>{nw->get(), rows, cols, cols, 1}, U.get(), S.get(), Vt.get(), st,
+                   kSvdRight);
+        }
         std::vector<double> hs = host_copy(S.get(), kk);
         ps_svd.reset();
         int keep = truncation_rank_rel(hs, move_tol(tol, prec) / std::sqrt((double)d), cap);
