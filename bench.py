@@ -474,6 +474,7 @@ def run_ours(a):
     cflops, csec = tg.contraction_stats()
     tflops, tsec, tlaunch = tg.tc_stats()
     lflops, lsec, lcalls = tg.lu_stats()
+    gflops64, gsec64, glaunch64 = tg.gemm64_stats()
     reached = ttg is not None
     ttg_all, total = max_over_ranks([ttg if reached else float("inf"), total], device="cuda")
     head = _form_record(infos, ttg, total, p_star)
@@ -552,7 +553,15 @@ def run_ours(a):
         peak_note = f"{peak_kind} bf16 sustained x {ratio} (nominal dtype ratio)"
     contraction_tflops = cflops / csec / 1e12 if csec > 0 else 0.0
     lu_tflops = lflops / lsec / 1e12 if lsec > 0 else 0.0
-    if lsec > csec and a.precision == "fp64":
+    if a.precision == "fp64" and gsec64 > lsec and gsec64 > 0:
+        # the FP64 strided GEMM kernel (every FP64 contraction stage, local
+        # operator and block move) takes the most device time
+        achieved = gflops64 / gsec64 / 1e12
+        kernel = (f"gemm_nd_kernel<double> (FP64 strided SIMT GEMM of the contraction stages, local operators, "
+                  f"block moves and trailing updates): {glaunch64} launches, "
+                  f"{gflops64 / max(glaunch64, 1) / 1e6:.3f} MFLOP and {gsec64 / max(glaunch64, 1) * 1e6:.1f} us "
+                  f"per launch")
+    elif lsec > csec and a.precision == "fp64":
         # the dense local solves take most of the FP64 iteration: block
         # elimination (bordered Cholesky, Schur-complement LU, cluster
         # triangular solves); when most of them kept FP32 factors (refined to
@@ -592,6 +601,8 @@ def run_ours(a):
         "lu_systems": lcalls,
         "local_solves": {"systems": lcalls, "block_elimination": kkt_block, "fp32_factors_refined": kkt_fp32,
                          "lu_fallbacks": kkt_lu},
+        "gemm64": {"launches": glaunch64, "tflops": gflops64 / gsec64 / 1e12 if gsec64 > 0 else 0.0,
+                   "seconds": gsec64, "share": gsec64 / total if total > 0 else None},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
                      "frac": achieved / peak if peak else None, "traffic": None, "peak_source": peak_note,
                      "kernel": kernel},

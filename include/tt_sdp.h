@@ -226,8 +226,9 @@ typedef struct {
   int32_t eig_rank;    /* TT rank of the step-length eigenvector                       */
   int32_t eig_sweeps;
   uint64_t seed;       /* SplitMix64 counter stream seed                               */
-  int32_t local_dense_max; /* reduced local systems up to this size are solved by LU,
-                              larger ones matrix-free by restarted GMRES             */
+  int32_t local_dense_max; /* reduced local systems up to this size (8192) are formed
+                              and solved by block elimination (or LU), larger ones
+                              matrix-free by restarted GMRES                       */
   int32_t gmres_restart;
   int32_t gmres_max_iters; /* operator products per local solve                       */
   int32_t eig_two_site;    /* step lengths (Section 3.4): 1 two-site DMRG sweeps with
@@ -532,6 +533,12 @@ void tt_tc_stats(double* flops, double* seconds, uint64_t* launches);
  * fallback includes the block attempt). Reset with
  * tt_contraction_stats_reset. */
 void tt_lu_stats(double* flops, double* seconds, uint64_t* calls);
+/* FP64 launches of the strided SIMT GEMM (gemm_nd_kernel: every FP64
+ * contraction stage, local operator, block move and trailing update) since
+ * the last reset: algorithmic flops (2 M N K), device seconds from CUDA events
+ * around each launch (its split-K reduction included) and the launch count.
+ * Reset with tt_contraction_stats_reset. */
+void tt_gemm64_stats(double* flops, double* seconds, uint64_t* launches);
 /* Per-phase host wall time accumulated while the environment variable
  * TTSDP_PROFILE=1 is set (each phase then synchronises the stream): one
  * "name seconds" line per phase, written NUL-terminated into buf (at most cap

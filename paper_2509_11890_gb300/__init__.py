@@ -543,6 +543,13 @@ def profile_report() -> dict:
     return out
 
 
+def gemm64_stats():
+    """(flops, seconds, launches) of the FP64 strided GEMM launches since the last reset."""
+    f, s, n = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_uint64(0)
+    lib().tt_gemm64_stats(ctypes.byref(f), ctypes.byref(s), ctypes.byref(n))
+    return f.value, s.value, n.value
+
+
 def lu_stats():
     """(flops, seconds, systems) of the dense local LU solves since the last reset."""
     f, s, n = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_uint64(0)

@@ -133,6 +133,7 @@ SIGNATURES = {
     "tt_sdp_get_trace": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_size_t)]),
     "tt_tc_stats": (None, [P_double, P_double, ctypes.POINTER(ctypes.c_uint64)]),
     "tt_lu_stats": (None, [P_double, P_double, ctypes.POINTER(ctypes.c_uint64)]),
+    "tt_gemm64_stats": (None, [P_double, P_double, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 _LIB = None

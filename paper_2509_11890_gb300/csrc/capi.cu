@@ -214,6 +214,18 @@ void tt_tc_stats(double* flops, double* seconds, uint64_t* launches) {
   }
 }
 
+void tt_gemm64_stats(double* flops, double* seconds, uint64_t* launches) {
+  try {
+    unsigned long long c = 0;
+    stats_read(flops, seconds, 3, &c);
+    if (launches) *launches = c;
+  } catch (...) {
+    if (flops) *flops = 0;
+    if (seconds) *seconds = 0;
+    if (launches) *launches = 0;
+  }
+}
+
 void tt_lu_stats(double* flops, double* seconds, uint64_t* calls) {
   try {
     unsigned long long c = 0;
@@ -415,7 +427,7 @@ void tt_sdp_default_options(tt_sdp_options* o) {
   o->eig_rank = 4;
   o->eig_sweeps = 4;
   o->seed = 1234;
-  o->local_dense_max = 4096;
+  o->local_dense_max = 8192;
   o->gmres_restart = 40;
   o->gmres_max_iters = 400;
   o->eig_two_site = 1;

@@ -32,7 +32,7 @@ void to_f64(const float* a, double* b, size_t n, cudaStream_t st);
 // Statistics of timed work (device time via CUDA events and algorithmic
 // flops). key 0: whole contraction calls; key 1: tensor-core GEMM launches;
 // key 2: LU factorisations and solves of the dense local systems.
-constexpr int kStatKeys = 3;
+constexpr int kStatKeys = 4;  // contractions, tensor-core GEMMs, dense local solves, FP64 strided GEMMs
 void stats_begin(cudaStream_t st, int key = 0);
 void stats_end(cudaStream_t st, double flops, int key = 0);
 void stats_read(double* flops, double* seconds, int key = 0, unsigned long long* calls = nullptr);

@@ -6,6 +6,7 @@
 // an element is one add; out-of-range rows / columns / k read zero.
 #include <algorithm>
 
+#include "contract.cuh"
 #include "gemm.cuh"
 
 namespace ttsdp {
@@ -263,6 +264,9 @@ void gemm_nd(const GemmND& g, const T* A, size_t nA, const T* B, size_t nB, T* C
   DBuf<T> work;
   if (ksplit > 1) work.alloc((size_t)Bt * ksplit * Mt * Nt);
   dim3 grid((unsigned)((Nt + BN - 1) / BN), (unsigned)((Mt + BM - 1) / BM), (unsigned)(Bt * ksplit));
+  // FP64 launches are timed (CUDA events) and counted with 2 M N K flops
+  constexpr bool kTimed = std::is_same<T, double>::value;
+  if (kTimed) stats_begin(st, 3);
   gemm_nd_kernel<T><<<grid, NT, 0, st>>>(d, A, B, C, alpha, beta, (int)Mt, (int)Nt, (int)Kt, ksplit, kchunk,
                                          work.get());
   count_launch();
@@ -274,6 +278,7 @@ void gemm_nd(const GemmND& g, const T* A, size_t nA, const T* B, size_t nB, T* C
     count_launch();
     check_launch("split_reduce_kernel");
   }
+  if (kTimed) stats_end(st, 2.0 * (double)Mt * (double)Nt * (double)Kt * (double)Bt, 3);
 }
 
 namespace {

@@ -45,7 +45,7 @@ struct Options {
   int eig_two_site = 1;  // step lengths by two-site DMRG sweeps; 0: one-site ALS
   double time_limit = 0.0;  // seconds per solve (0: none)
   uint64_t seed = 1234;
-  int local_dense_max = 4096, gmres_restart = 40, gmres_max_iters = 400;
+  int local_dense_max = 8192, gmres_restart = 40, gmres_max_iters = 400;
   int combined_multipliers = 1;  // one block dLambda for dY, dT when their masks are disjoint
   // finishing phase (Section 3.5): absolute tolerance (0: off) and the barrier relaxation range
   double finish_tol = 0.0, nu0 = 1e-6, nu_max = 1e-3;
