@@ -374,7 +374,8 @@ tt_status tt_lu_solve(int32_t n, const double* K, double* b, int32_t precision, 
  * FP64 factors (at most three steps towards 1e-15). Reduced precisions: FP32
  * factors and at most five steps towards 1e-10. When L_Z is not numerically
  * positive definite, or the residual stays above 1e-10, the whole system is
- * solved as tt_lu_solve does. b (n doubles, device) is overwritten by x; *rel_residual
+ * solved by LU with partial pivoting: FP32 factors refined in FP64 (kept in
+ * TT_FP64 only at a residual of 1e-14), else, in TT_FP64, FP64 factors. b (n doubles, device) is overwritten by x; *rel_residual
  * (host) receives the FP64 relative residual. 0 < n_lz < n is required.
  * Synchronises the stream. */
 tt_status tt_kkt_solve(int32_t n, int32_t n_lz, const double* K, double* b, int32_t precision,
