@@ -536,9 +536,10 @@ void tt_tc_stats(double* flops, double* seconds, uint64_t* launches);
 void tt_lu_stats(double* flops, double* seconds, uint64_t* calls);
 /* FP64 launches of the strided SIMT GEMM (gemm_nd_kernel: every FP64
  * contraction stage, local operator, block move and trailing update) since
- * the last reset: algorithmic flops (2 M N K), device seconds from CUDA events
- * around each launch (its split-K reduction included) and the launch count.
- * Reset with tt_contraction_stats_reset. */
+ * the last reset, sampled: every eighth launch of each host thread is timed
+ * with CUDA events (its split-K reduction included); flops (2 M N K),
+ * seconds and the count are those of the timed launches (about an eighth of
+ * all). Reset with tt_contraction_stats_reset. */
 void tt_gemm64_stats(double* flops, double* seconds, uint64_t* launches);
 /* Per-phase host wall time accumulated while the environment variable
  * TTSDP_PROFILE=1 is set (each phase then synchronises the stream): one
