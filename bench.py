@@ -367,6 +367,63 @@ def _solve_timed(tg, torch, wcores, opts, steps, stream, clocks=None):
     return infos, total, ttg, tg.launch_count() - l0
 
 
+def roofline_choice(precision, peaks, peak_kind, contraction, tc, local, gemm64):
+    """The bench line's roofline kernel: the one with the most device time in
+    the timed region, with its own achieved rate and peak. contraction =
+    (flops, seconds) of the contraction stages; tc = (flops, seconds,
+    launches) of the tcgen05 GEMM; local = (flops, seconds, systems, systems
+    with FP32 factors, LU fallbacks) of the dense local solves; gemm64 =
+    (flops, seconds, launches) of the timed FP64 strided GEMM launches (every
+    eighth). Returns (bound, achieved, peak, unit, peak_note, kernel)."""
+    cflops, csec = contraction
+    tflops, tsec, tlaunch = tc
+    lflops, lsec, lcalls, kkt_fp32, kkt_lu = local
+    gflops64, gsec64, glaunch64 = gemm64
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if precision == "fp64":
+        bound, peak, punit = "alu", 1.25, "TFLOP/s"  # FP64 FMA rate of GB300 (nominal; 1.2547 measured)
+        peak_note = "FP64 ALU peak, nominal 1.25 TFLOP/s (probe measured 1.25)"
+    elif precision == "fp32":
+        bound, peak, punit = "alu", fp32_peak, "TFLOP/s"
+        peak_note = "FP32 ALU peak from 152 SMs x 128 lanes x 2 flops x max SM clock"
+    else:
+        ratio = 0.5 if precision == "tf32" else 1.0
+        bound, peak, punit = "tensor", peaks["bf16_tflops_sustained"] * ratio, "TFLOP/s"
+        peak_note = f"{peak_kind} bf16 sustained x {ratio} (nominal dtype ratio)"
+    if precision == "fp64" and 8 * gsec64 > lsec and gsec64 > 0:
+        # the FP64 strided GEMM kernel (every FP64 contraction stage, local
+        # operator and block move) takes the most device time
+        achieved = gflops64 / gsec64 / 1e12
+        kernel = (f"gemm_nd_kernel<double> (FP64 strided SIMT GEMM of the contraction stages, local operators, "
+                  f"block moves and trailing updates): {glaunch64} timed launches (every eighth), "
+                  f"{gflops64 / max(glaunch64, 1) / 1e6:.3f} MFLOP and {gsec64 / max(glaunch64, 1) * 1e6:.1f} us "
+                  f"per launch")
+    elif lsec > csec and precision == "fp64":
+        # the dense local solves take most of the FP64 iteration: block
+        # elimination (bordered Cholesky, Schur-complement LU, cluster
+        # triangular solves); when most of them kept FP32 factors (refined to
+        # an FP64 residual of 1e-14) their peak is the FP32 ALU rate
+        achieved = lflops / lsec / 1e12
+        if kkt_fp32 * 2 > max(lcalls, 1):
+            peak = fp32_peak
+            peak_note = ("FP32 ALU peak from 152 SMs x 128 lanes x 2 flops x max SM clock (most local solves "
+                         "factored in FP32 and refined in FP64)")
+        kernel = (f"dense local solves (block elimination: bordered Cholesky, Schur-complement LU, cluster "
+                  f"triangular solves; {kkt_fp32} of {lcalls} with FP32 factors refined in FP64, "
+                  f"{kkt_lu} LU fallbacks): {lflops / max(lcalls, 1) / 1e9:.4f} GFLOP and "
+                  f"{lsec / max(lcalls, 1) * 1e3:.3f} ms per system")
+    elif bound == "tensor":
+        # the tensor-core kernel: tcgen05 GEMM of the contraction stages
+        achieved = tflops / tsec / 1e12 if tsec > 0 else 0.0
+        kernel = (f"tc_gemm_kernel (tcgen05 {precision.upper()} GEMM of the contractions): "
+                  f"{tlaunch} launches, {tflops / max(tlaunch, 1) / 1e9:.4f} GFLOP and "
+                  f"{tsec / max(tlaunch, 1) * 1e6:.1f} us per launch")
+    else:
+        achieved = cflops / csec / 1e12 if csec > 0 else 0.0
+        kernel = "environment / local-product contraction (three strided SIMT GEMM stages)"
+    return bound, achieved, peak, punit, peak_note, kernel
+
+
 def _form_record(infos, ttg, total, p_star):
     conv = [i for i in infos if i["converged"]]
     last = conv[0] if conv else infos[-1]
@@ -541,49 +598,11 @@ def run_ours(a):
                "d2h_bytes_per_step": int(sum(c.size for c in X) * 8), "steps": n_e2e,
                "gap_reached": bool(info["converged"]), "timed_s": e2e_t}
     peaks, peak_kind = _peaks()
-    if a.precision == "fp64":
-        bound, peak, punit = "alu", 1.25, "TFLOP/s"  # FP64 FMA rate of GB300 (nominal; 1.2547 measured)
-        peak_note = "FP64 ALU peak, nominal 1.25 TFLOP/s (probe measured 1.25)"
-    elif a.precision == "fp32":
-        bound, peak, punit = "alu", 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
-        peak_note = "FP32 ALU peak from 152 SMs x 128 lanes x 2 flops x max SM clock"
-    else:
-        ratio = 0.5 if a.precision == "tf32" else 1.0
-        bound, peak, punit = "tensor", peaks["bf16_tflops_sustained"] * ratio, "TFLOP/s"
-        peak_note = f"{peak_kind} bf16 sustained x {ratio} (nominal dtype ratio)"
     contraction_tflops = cflops / csec / 1e12 if csec > 0 else 0.0
     lu_tflops = lflops / lsec / 1e12 if lsec > 0 else 0.0
-    if a.precision == "fp64" and 8 * gsec64 > lsec and gsec64 > 0:
-        # the FP64 strided GEMM kernel (every FP64 contraction stage, local
-        # operator and block move) takes the most device time
-        achieved = gflops64 / gsec64 / 1e12
-        kernel = (f"gemm_nd_kernel<double> (FP64 strided SIMT GEMM of the contraction stages, local operators, "
-                  f"block moves and trailing updates): {glaunch64} timed launches (every eighth), "
-                  f"{gflops64 / max(glaunch64, 1) / 1e6:.3f} MFLOP and {gsec64 / max(glaunch64, 1) * 1e6:.1f} us "
-                  f"per launch")
-    elif lsec > csec and a.precision == "fp64":
-        # the dense local solves take most of the FP64 iteration: block
-        # elimination (bordered Cholesky, Schur-complement LU, cluster
-        # triangular solves); when most of them kept FP32 factors (refined to
-        # an FP64 residual of 1e-14) their peak is the FP32 ALU rate
-        achieved = lu_tflops
-        if kkt_fp32 * 2 > max(lcalls, 1):
-            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            peak_note = ("FP32 ALU peak from 152 SMs x 128 lanes x 2 flops x max SM clock (most local solves "
-                         "factored in FP32 and refined in FP64)")
-        kernel = (f"dense local solves (block elimination: bordered Cholesky, Schur-complement LU, cluster "
-                  f"triangular solves; {kkt_fp32} of {lcalls} with FP32 factors refined in FP64, "
-                  f"{kkt_lu} LU fallbacks): {lflops / max(lcalls, 1) / 1e9:.4f} GFLOP and "
-                  f"{lsec / max(lcalls, 1) * 1e3:.3f} ms per system")
-    elif bound == "tensor":
-        # the tensor-core kernel: tcgen05 GEMM of the contraction stages
-        achieved = tflops / tsec / 1e12 if tsec > 0 else 0.0
-        kernel = (f"tc_gemm_kernel (tcgen05 {a.precision.upper()} GEMM of the contractions): "
-                  f"{tlaunch} launches, {tflops / max(tlaunch, 1) / 1e9:.4f} GFLOP and "
-                  f"{tsec / max(tlaunch, 1) * 1e6:.1f} us per launch")
-    else:
-        achieved = contraction_tflops
-        kernel = "environment / local-product contraction (three strided SIMT GEMM stages)"
+    bound, achieved, peak, punit, peak_note, kernel = roofline_choice(
+        a.precision, peaks, peak_kind, contraction=(cflops, csec), tc=(tflops, tsec, tlaunch),
+        local=(lflops, lsec, lcalls, kkt_fp32, kkt_lu), gemm64=(gflops64, gsec64, glaunch64))
     line = {
         "metric": "time-to-gap-1e-4 (s)", "value": ttg_all if reached else None, "unit": "s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": total / a.steps * 1e3, "higher_is_better": False,

@@ -85,3 +85,29 @@ def test_dual_residual_bound_is_zero_for_low_rank_objectives():
     from paper_2509_11890_gb300 import inputs
     lb = bench.dual_residual_lower_bound(inputs.maxcut_kron(8, 0)["weights"], 16)
     assert lb["rel_d_lower_bound"] < 1e-12 and lb["certifiable"]
+
+
+def test_roofline_choice_names_the_kernel_with_the_most_device_time():
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    peaks = {"bf16_tflops_sustained": 1716.8, "sm_max_mhz": 2070.0}
+    zero3 = (0.0, 0.0, 0)
+    # FP64: eight times the sampled GEMM time above the local solves' time -> the GEMM kernel, FP64 peak
+    r = bench.roofline_choice("fp64", peaks, "measured", contraction=(1e9, 0.5), tc=zero3,
+                              local=(4e11, 0.6, 260, 224, 36), gemm64=(1.6e10, 0.2, 4000))
+    assert r[0] == "alu" and r[2] == 1.25 and r[5].startswith("gemm_nd_kernel<double>")
+    assert abs(r[1] - 1.6e10 / 0.2 / 1e12) < 1e-12
+    # FP64 with the local solves leading and most of them on FP32 factors -> the FP32 ALU peak
+    r = bench.roofline_choice("fp64", peaks, "measured", contraction=(1e9, 0.5), tc=zero3,
+                              local=(4e11, 2.0, 260, 224, 36), gemm64=(1.6e10, 0.2, 4000))
+    assert r[5].startswith("dense local solves") and abs(r[2] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    # ... and on FP64 factors -> the FP64 peak
+    r = bench.roofline_choice("fp64", peaks, "measured", contraction=(1e9, 0.5), tc=zero3,
+                              local=(4e11, 2.0, 260, 10, 0), gemm64=(1.6e10, 0.2, 4000))
+    assert r[2] == 1.25
+    # TF32: the tensor-core GEMM against half the BF16 sustained peak
+    r = bench.roofline_choice("tf32", peaks, "measured", contraction=(1e9, 0.5), tc=(2e12, 0.01, 100),
+                              local=(4e11, 0.1, 260, 260, 0), gemm64=zero3)
+    assert r[0] == "tensor" and abs(r[2] - 858.4) < 1e-9 and r[5].startswith("tc_gemm_kernel")
+    assert abs(r[1] - 200.0) < 1e-9
