@@ -518,10 +518,54 @@ struct AmenInfo {
                                // reduced precision: max(tol, the precision's floor))
 };
 
+// H[i][j] += h[i] for i <= j (H: (m + 1) x m row-major)
+__global__ void hess_accum_kernel(double* H, int m, int j, const double* h) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= j) H[(size_t)i * m + j] += h[i];
+}
+
+// The bookkeeping of Arnoldi step j on the device (one thread): the new
+// subdiagonal entry sqrt(*nrm2), the earlier Givens rotations applied to
+// column j, the new rotation and the rotated right-hand side g; out[0] =
+// |g[j+1]| (the residual norm of the least-squares solution), out[1] = the
+// subdiagonal entry, *inv = its inverse (0 when it is 0).
+__global__ void arnoldi_step_kernel(double* H, int m, int j, double* cs, double* sn, double* g, const double* nrm2,
+                                    double* inv, double* out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const double hn = sqrt(fmax(*nrm2, 0.0));
+  H[(size_t)(j + 1) * m + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+    H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+    H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+  }
+  const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+  const double rr = hypot(a, c);
+  cs[j] = rr > 0 ? a / rr : 1.0;
+  sn[j] = rr > 0 ? c / rr : 0.0;
+  H[(size_t)j * m + j] = rr;
+  H[(size_t)(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  out[0] = fabs(g[j + 1]);
+  out[1] = hn;
+  *inv = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
+// y = x * (*s) with the scalar read on the device
+__global__ void scale_by_dev_kernel(const double* x, long long n, const double* s, double* y) {
+  const double v = *s;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] * v;
+}
+
 // Restarted GMRES (Saad & Schultz) on device vectors with classical
-// Gram-Schmidt applied twice and Givens rotations on the host-side Hessenberg
-// matrix. Stops at ||b - A x|| <= tol ||b|| or after maxit products. Returns
-// the number of operator products.
+// Gram-Schmidt applied twice. The Hessenberg matrix, its Givens rotations and
+// the rotated right-hand side stay on the device, so an Arnoldi step reads
+// back one pair of scalars (the residual estimate and the subdiagonal entry)
+// instead of the projections and the norm; the small triangular solve of a
+// cycle runs on the host. Stops at ||b - A x|| <= tol ||b|| or after maxit
+// products. Returns the number of operator products.
 int gmres(size_t N, const std::function<void(const double*, double*)>& A, const double* b, double* x, double tol,
           int m, int maxit) {
   cudaStream_t st = cur_stream();
@@ -530,8 +574,10 @@ int gmres(size_t N, const std::function<void(const double*, double*)>& A, const 
     dev_fill(x, N, 0.0, st);
     return 0;
   }
-  DBuf<double> V((size_t)(m + 1) * N), w(N), hdev(m + 1);
-  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
+  DBuf<double> V((size_t)(m + 1) * N), w(N), hdev(m + 1), Hd((size_t)(m + 1) * m), csd(m), snd(m), gd(m + 1),
+      scal(2), stat(2);
+  std::vector<double> H((size_t)(m + 1) * m), g(m + 1);
+  const int grid = (int)std::min<long long>(((long long)N + 255) / 256, 152 * 8);
   int total = 0;
   while (total < maxit) {
     A(x, w.get());
@@ -541,9 +587,9 @@ int gmres(size_t N, const std::function<void(const double*, double*)>& A, const 
     if (beta <= tol * bnorm) break;
     dev_copy(V.get(), w.get(), N, st);
     dev_scale(V.get(), N, 1.0 / beta, st);
-    std::fill(g.begin(), g.end(), 0.0);
-    std::fill(H.begin(), H.end(), 0.0);
-    g[0] = beta;
+    dev_fill(Hd.get(), (size_t)(m + 1) * m, 0.0, st);
+    dev_fill(gd.get(), m + 1, 0.0, st);
+    dev_fill(gd.get(), 1, beta, st);
     int jl = -1;
     bool done = false;
     for (int j = 0; j < m && total < maxit; ++j) {
@@ -551,44 +597,36 @@ int gmres(size_t N, const std::function<void(const double*, double*)>& A, const 
       ++total;
       for (int pass = 0; pass < 2; ++pass) {
         dev_multi_dot(V.get(), j + 1, N, w.get(), hdev.get(), st);
-        std::vector<double> h(j + 1);
-        TT_CUDA(cudaMemcpyAsync(h.data(), hdev.get(), (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-        TT_CUDA(sync_stream(st));
-        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
+        hess_accum_kernel<<<(j + 1 + 127) / 128, 128, 0, st>>>(Hd.get(), m, j, hdev.get());
+        count_launch();
         gemm_rm<double>(true, false, (int)N, 1, j + 1, -1.0, V.get(), (int)N, 0, hdev.get(), 1, 0, 1.0, w.get(), 1, 0,
                         1, st);
       }
-      const double hn = dev_norm(w.get(), N);
-      H[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0) {
-        dev_copy(V.get() + (size_t)(j + 1) * N, w.get(), N, st);
-        dev_scale(V.get() + (size_t)(j + 1) * N, N, 1.0 / hn, st);
-      }
-      for (int i = 0; i < j; ++i) {
-        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
-      }
-      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-      const double rr = std::hypot(a, c);
-      cs[j] = rr > 0 ? a / rr : 1.0;
-      sn[j] = rr > 0 ? c / rr : 0.0;
-      H[(size_t)j * m + j] = rr;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
+      dev_dot_async(w.get(), w.get(), N, scal.get(), st);
+      arnoldi_step_kernel<<<1, 32, 0, st>>>(Hd.get(), m, j, csd.get(), snd.get(), gd.get(), scal.get(),
+                                             scal.get() + 1, stat.get());
+      scale_by_dev_kernel<<<grid, 256, 0, st>>>(w.get(), (long long)N, scal.get() + 1, V.get() + (size_t)(j + 1) * N);
+      count_launch();
+      count_launch();
+      check_launch("gmres arnoldi step");
+      double hs[2] = {0.0, 0.0};
+      TT_CUDA(cudaMemcpyAsync(hs, stat.get(), sizeof(hs), cudaMemcpyDeviceToHost, st));
+      TT_CUDA(sync_stream(st));
       jl = j;
-      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) {
+      if (hs[0] <= tol * bnorm || hs[1] == 0.0) {
         done = true;
         break;
       }
     }
     if (jl < 0) break;
+    TT_CUDA(cudaMemcpyAsync(H.data(), Hd.get(), H.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(cudaMemcpyAsync(g.data(), gd.get(), g.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TT_CUDA(sync_stream(st));
     std::vector<double> y(jl + 1, 0.0);
     for (int i = jl; i >= 0; --i) {
-      double s = g[i];
-      for (int t2 = i + 1; t2 <= jl; ++t2) s -= H[(size_t)i * m + t2] * y[t2];
-      y[i] = H[(size_t)i * m + i] != 0.0 ? s / H[(size_t)i * m + i] : 0.0;
+      double sum = g[i];
+      for (int t2 = i + 1; t2 <= jl; ++t2) sum -= H[(size_t)i * m + t2] * y[t2];
+      y[i] = H[(size_t)i * m + i] != 0.0 ? sum / H[(size_t)i * m + i] : 0.0;
     }
     upload(hdev.get(), y);
     gemm_rm<double>(true, false, (int)N, 1, jl + 1, 1.0, V.get(), (int)N, 0, hdev.get(), 1, 0, 1.0, x, 1, 0, 1, st);

@@ -322,10 +322,9 @@ void dev_multi_dot(const double* V, int nvec, size_t N, const double* w, double*
   check_launch("multi_dot");
 }
 
-double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st) {
-  DBuf<double> out(1);
+void dev_dot_async(const double* a, const double* b, size_t n, double* out, cudaStream_t st) {
   if (n < (size_t(1) << 16)) {
-    dot_kernel<<<1, 1024, 0, st>>>(a, b, (long long)n, out.get());
+    dot_kernel<<<1, 1024, 0, st>>>(a, b, (long long)n, out);
     count_launch();
   } else {
     // long vectors (GMRES bases of large local systems): partial sums on many
@@ -334,11 +333,16 @@ double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st) {
     const int G = (int)(chunks < 304 ? chunks : 304);
     DBuf<double> part((size_t)G);
     dot_partial_kernel<<<G, 1024, 0, st>>>(a, b, (long long)n, part.get());
-    dot_kernel<<<1, 1024, 0, st>>>(part.get(), nullptr, -(long long)G, out.get());
+    dot_kernel<<<1, 1024, 0, st>>>(part.get(), nullptr, -(long long)G, out);
     count_launch();
     count_launch();
   }
   check_launch("dot");
+}
+
+double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st) {
+  DBuf<double> out(1);
+  dev_dot_async(a, b, n, out.get(), st);
   double h = 0.0;
   TT_CUDA(cudaMemcpyAsync(&h, out.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_CUDA(sync_stream(st));

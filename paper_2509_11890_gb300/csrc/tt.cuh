@@ -118,6 +118,8 @@ void dev_copy2d(double* dst, long long dld, const double* src, long long sld, in
 void dev_scale_rows(double* a, int rows, int cols, const double* s, cudaStream_t st);
 void dev_scale_cols(double* a, int rows, int cols, const double* s, cudaStream_t st);
 double dev_dot(const double* a, const double* b, size_t n, cudaStream_t st);
+// *out (device) = a . b, left on the device (no host synchronisation)
+void dev_dot_async(const double* a, const double* b, size_t n, double* out, cudaStream_t st);
 // out[i] = <V_i, w> for the rows of a row-major nvec x N matrix (device output)
 void dev_multi_dot(const double* V, int nvec, size_t N, const double* w, double* out, cudaStream_t st);
 
