@@ -974,10 +974,13 @@ def run_micro_contract(a):
     configured workloads: frame and vector ranks r, operator ranks R, modes
     4 x 4, with (r, R) = (16, 32), (64, 128), (128, 256). CUDA events on the
     launching stream around `steps` calls after `warmup`; algorithmic flops
-    of the three stages (the library's own count)."""
+    of the three stages (the library's own count). Beside each shape, the
+    oracle's environment update (numpy einsum chain, FP64) timed on the host
+    cores: the CPU baseline of the contraction throughput."""
     import torch
 
     import paper_2509_11890_gb300 as tg
+    from oracle import tt as ott
     from paper_2509_11890_gb300 import inputs
 
     torch.cuda.set_device(0)
@@ -991,6 +994,20 @@ def run_micro_contract(a):
         out = torch.empty(r * R * r, dtype=torch.float64, device="cuda")
         y = torch.empty(r * 4 * r, dtype=torch.float64, device="cuda")
         flops = (2.0 * r * R * r * 4 * r + 2.0 * r * r * (R * 4) * (4 * R) + 2.0 * r * R * r * r * 4)
+        # CPU baseline: the oracle's update of the same operands, best of a few calls
+        hp, hu, hop, hv = (x.cpu().numpy() for x in (phi, u, op, v))
+        times = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            ott.env_left_step(hp, hu, hop, hv)
+            times.append(time.perf_counter() - t0)
+            if sum(times) > 10.0:
+                break
+        cpu_s = min(times)
+        print(json.dumps({"micro": "env_left (oracle, numpy einsum chain)", "r": r, "R": R, "precision": "fp64",
+                          "seconds": cpu_s, "gflop": flops / 1e9, "tflops": flops / cpu_s / 1e12,
+                          "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(),
+                                           "sample": f"best of {len(times)} calls"}}), flush=True)
         for pn in ("fp64", "fp32", "tf32", "bf16"):
             for name, fn in (("env_left", lambda: tg.env_left_step(dims, phi, u, op, v, out, PREC[pn])),
                              ("env_right", lambda: tg.env_right_step(dims, psi, u, op, v, out, PREC[pn])),
